@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 FX correlator on the 10-station space-VLBI scan.
+
+Workload: 10 stations (1 spacecraft + 9 ground), 8 subbands x 16 MHz x 2 pols
+(32 Msample/s real, 2-bit), a 10 s scan, 1024 channels (2048-point FFTs),
+1 s integrations, quintic delay segments (spacecraft delay ~0.3-1.2 s, rate up
+to 3e-5 s/s; ground delays up to 20 ms), a segment boundary inside the scan.
+One step correlates the whole scan (all 10 integrations) through the C ABI.
+
+  value  station-samples/s with the packed samples already in device memory
+         (corr_attach_samples_device + corr_correlate_device), timed with CUDA
+         events on the library's stream over K steps;
+  e2e    the same metric through the host API: every step pushes all stations'
+         packed bytes from pinned host memory (corr_push_samples) and reads
+         every integration back to host memory (corr_correlate).
+
+A station-sample is one real 2-bit sample of one stream (station x subband x
+pol).  Inputs (14 GB) exceed the 129 MB L2, so no flush is needed between
+steps.  Synthetic data: independent 2-bit quantised Gaussian noise (codes
+drawn with the probabilities of +-0.98 sigma quantisation) made on the device
+from a seeded generator; the correlator's cost does not depend on the values.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample (the first 0.1 s of the same scan, one 0.1 s integration).
+Multi-GPU (torchrun): independent replicas, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "cfg2: 10 stations (1 space + 9 ground), 8 subbands x 16 MHz, 2 pols, 2-bit, 10 s, 1024 channels, 1 s integrations"
+METRIC = "station-samples/s"
+CPU_SAMPLE_S = 0.1
+# 2-bit code probabilities of +-0.98 sigma quantisation of a unit Gaussian
+P_OUTER = 0.5 * (1.0 - 0.6729121)
+FALLBACK_HBM_GBS = 6800.0
+SM_COUNT, FP32_LANES, MAX_SM_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--seed", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "copy_gbs"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def device_codes(nbytes: int, gen, device):
+    """Packed bytes of independent 2-bit codes with the quantised-Gaussian
+    code probabilities, made on the device in chunks."""
+    import torch
+    out = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    t1 = int(round(P_OUTER * 65536))
+    t2 = 32768
+    t3 = 65536 - t1
+    chunk = 1 << 26
+    for o in range(0, nbytes, chunk):
+        n = min(chunk, nbytes - o)
+        u = torch.randint(0, 65536, (n, 4), generator=gen, device=device, dtype=torch.int32)
+        c = (u >= t1).to(torch.uint8) + (u >= t2).to(torch.uint8) + (u >= t3).to(torch.uint8)
+        out[o:o + n] = c[:, 0] | (c[:, 1] << 2) | (c[:, 2] << 4) | (c[:, 3] << 6)
+    return out
+
+
+def make_scan(seed):
+    import synth
+    return synth.config2(seed=seed, duration=10.0, tint=1.0, boundary=5.0)
+
+
+def samples_per_step(scan):
+    return scan.stations * scan.G * int(round(scan.duration / scan.tint)) * int(round(scan.fs * scan.tint))
+
+
+def cpu_oracle_sample(scan, host_streams, threads_hint=None):
+    """Time the FP64 oracle on the first CPU_SAMPLE_S seconds of the scan as
+    one integration (all stations and streams).  Returns (samples/s, cores, secs)."""
+    import oracle
+    spi = int(round(scan.fs * CPU_SAMPLE_S))
+    ns = []
+    streams = []
+    for s in range(scan.stations):
+        n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
+        ns.append(n)
+        streams.append(np.ascontiguousarray(host_streams[s][: n * scan.G // 4]))
+    o = oracle.Oracle(scan.stations, scan.nsub, scan.npol, scan.nchan, scan.fs, CPU_SAMPLE_S, scan.nu0,
+                      scan.polys, streams, scan.sample0, ns)
+    t0 = time.perf_counter()
+    vis, w = o.correlate(0, 1)
+    dt = time.perf_counter() - t0
+    nblk = -(-spi // scan.N)
+    samples = scan.stations * scan.G * nblk * scan.N
+    cores = min(oracle.threads(), scan.G)
+    return samples / dt, cores, dt, float(w.min())
+
+
+def host_stream_prefix(dev_streams, scan):
+    spi = int(round(scan.fs * CPU_SAMPLE_S))
+    out = []
+    for s, t in enumerate(dev_streams):
+        n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
+        out.append(t[: n * scan.G // 4].cpu().numpy())
+    return out
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import torch
+    scan = make_scan(args.seed)
+    gen = torch.Generator(device="cpu")
+    gen.manual_seed(args.seed)
+    spi = int(round(scan.fs * CPU_SAMPLE_S))
+    streams = []
+    for s in range(scan.stations):
+        n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
+        streams.append(device_codes(n * scan.G // 4, gen, "cpu").numpy())
+    for _ in range(args.warmup):
+        cpu_oracle_sample(scan, streams)
+    rates, secs = [], []
+    cores = 1
+    for _ in range(args.steps):
+        r, cores, dt, _ = cpu_oracle_sample(scan, streams)
+        rates.append(r)
+        secs.append(dt)
+    value = float(np.mean(rates))
+    sample = "first %.1f s of the %s scan as one integration (all 10 stations, 16 streams)" % (CPU_SAMPLE_S, "cfg2")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1502_06894_gb300 import _build
+    _build.build()
+    from paper_1502_06894_gb300 import corr
+
+    scan = make_scan(args.seed + rank)
+    nint = int(round(scan.duration / scan.tint))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1000 + args.seed + rank)
+    dstreams = [device_codes(scan.nsamp[s] * scan.G // 4, gen, dev) for s in range(scan.stations)]
+    in_bytes = sum(int(t.numel()) for t in dstreams)
+    torch.cuda.synchronize()
+    # a dedicated stream: the library's launches and the timing events share it
+    stream = torch.cuda.Stream(device=dev)
+
+    c = corr.from_scan(scan, device_streams=dstreams)
+    c.set_stream(stream.cuda_stream)
+    c.flush()
+    out = torch.empty((nint, scan.nbl, scan.G, scan.nchan), dtype=torch.complex64, device=dev)
+    wts = torch.empty((nint, scan.nbl), dtype=torch.float64, device=dev)
+
+    def step():
+        c.rewind()
+        for i in range(nint):
+            rc = c.correlate_device(out[i], wts[i])
+            if rc != corr.CORR_OK:
+                raise RuntimeError("correlate_device returned %d" % rc)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    c.read_profile()
+    c.set_profiling(True)
+    clk = Clocks(dev.index)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    prof = c.read_profile()
+    c.set_profiling(False)
+    cb, kz = c.launch_shape()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sps = samples_per_step(scan)
+    value = sps * ws / (ms / 1e3)
+
+    # ---- roofline of the dominant kernel ----
+    peak_hbm, peak_src = measured_peaks()
+    S, G, N, nch = scan.stations, scan.G, scan.N, scan.nchan
+    nbl = scan.nbl
+    spi = int(round(scan.fs * scan.tint))
+    blocks_per_step = sum(-(-(i + 1) * spi // N) - (-(-i * spi // N)) for i in range(nint))
+    ss_step = blocks_per_step * S * G * N  # station-samples transformed per step
+    steps = args.steps
+    f_ms, f_n = prof["fstage"]
+    x_ms, x_n = prof["xstage"]
+    f_bytes = steps * ss_step * (0.25 + 4.0)
+    f_flops = steps * blocks_per_step * S * G * (2.5 * N * np.log2(N))
+    x_bytes = steps * (ss_step * 4.0 + (x_n / max(steps, 1)) * kz * nbl * G * nch * 16.0)
+    x_flops = steps * blocks_per_step * G * nch * nbl * 8.0
+    peak_alu = SM_COUNT * FP32_LANES * 2 * MAX_SM_MHZ * 1e6
+    stages = {}
+    for name, (tms, n) in prof.items():
+        stages[name] = {"ms_per_step": tms / steps, "launches_per_step": n / steps}
+    dom = "fstage" if f_ms >= x_ms else "xstage"
+    if dom == "fstage":
+        d_ms, d_n, d_bytes, d_flops = f_ms, f_n, f_bytes, f_flops
+    else:
+        d_ms, d_n, d_bytes, d_flops = x_ms, x_n, x_bytes, x_flops
+    t_launch = d_ms / 1e3 / max(d_n, 1)
+    gbs = d_bytes / max(d_n, 1) / t_launch / 1e9
+    tfl = d_flops / max(d_n, 1) / t_launch / 1e12
+    hbm_frac = gbs / peak_hbm
+    alu_frac = tfl * 1e12 / peak_alu
+    if hbm_frac >= alu_frac:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak_hbm, "unit": "GB/s", "frac": hbm_frac,
+                "traffic": None, "peak_source": peak_src}
+    else:
+        roof = {"bound": "alu", "achieved": tfl, "peak": peak_alu / 1e12, "unit": "TFLOP/s", "frac": alu_frac,
+                "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    roof.update({"kernel": "k_fstage<1024>" if dom == "fstage" else "k_xmac<10>",
+                 "bytes_per_launch": d_bytes / max(d_n, 1), "flops_per_launch": d_flops / max(d_n, 1),
+                 "launch_ms": t_launch * 1e3, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
+    launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
+    x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
+
+    # ---- end to end through the host API ----
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.empty(t.numel(), dtype=torch.uint8, pin_memory=True) for t in dstreams]
+        for h, t in zip(host, dstreams):
+            h.copy_(t)
+        c2 = corr.from_scan(scan)
+        for s in range(S):
+            c2.reserve(s, host[s].numel())
+        out_h = torch.empty((nint, nbl, G, nch), dtype=torch.complex64, pin_memory=True)
+        w_h = torch.empty((nint, nbl), dtype=torch.float64, pin_memory=True)
+
+        def e2e_step():
+            c2.reset()
+            for s in range(S):
+                c2.push(s, host[s])
+            c2.flush()
+            for i in range(nint):
+                rc = c2.correlate_into(out_h[i], w_h[i])
+                if rc != corr.CORR_OK:
+                    raise RuntimeError("corr_correlate returned %d" % rc)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ne = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ne):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ne
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        d2h = int(out_h[0].numel() * 8 * nint + w_h.numel() * 8)
+        e2e = {"value": sps * ws / dt, "unit": METRIC, "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
+               "ms_per_step": dt * 1e3, "steps": ne}
+        c2.close()
+
+    # ---- CPU oracle on a bounded sample ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        hs = host_stream_prefix(dstreams, scan)
+        r, cores, dt, wmin = cpu_oracle_sample(scan, hs)
+        cpu = {"value": r, "unit": METRIC, "cores": cores, "kind": "oracle",
+               "sample": "first %.1f s of the scan as one integration, all stations and streams (%.1f s wall)"
+                         % (CPU_SAMPLE_S, dt)}
+
+    c.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "stations": S, "subbands": scan.nsub, "pols": scan.npol,
+                           "nchan": nch, "fft": N, "duration_s": scan.duration, "tint_s": scan.tint,
+                           "station_samples_per_step": sps, "input_bytes": in_bytes,
+                           "l2": "inputs %.1f GB > 129 MB L2 (no flush needed)" % (in_bytes / 1e9),
+                           "chunk_blocks": cb, "x_partials": kz,
+                           "parallelism": "replicas x%d" % ws},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

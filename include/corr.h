@@ -1,0 +1,187 @@
+/*
+ * corr.h -- C ABI of the GB300 FX correlator library (libcorr.so).
+ *
+ * What it computes.  The paper (Bruni et al., "Space-VLBI with RadioAstron:
+ * new correlator capabilities at MPIfR", Abstract) describes DiFX as an FX
+ * correlator: every station's sampled voltage is Fourier transformed first,
+ * then each station pair is cross-multiplied and accumulated.  Its Sec. 2
+ * describes the dra version's delay model (Calc extended to a spacecraft
+ * with arbitrary position and velocity, general-relativistic terms, and the
+ * spacecraft -> tracking-station transmission leg) and the RadioAstron ->
+ * Mark5B data conversion.  Both enter this library only as inputs: per-station
+ * delay-polynomial segments (corr_set_delay_poly) and packed 2-bit sample
+ * streams (corr_push_samples).  Per FFT block and station the library
+ *   1. evaluates the delay polynomial in FP64 at the block centre and picks
+ *      the integer-sample window [b*N + n_b, +N), n_b = floor(tau*fs + 1/2);
+ *   2. unpacks the 2-bit samples of that window (4-entry level table);
+ *   3. takes the N-point real FFT and keeps channels k = 0..nchan-1 (N = 2*nchan);
+ *   4. multiplies by exp(+2 pi i (frac(nu0 tau) + k*fs/N * eps)), eps = tau - n_b/fs
+ *      (fractional-delay slope and fringe rotation, after the FFT);
+ *   5. accumulates V_ab[k] += X_a[k] conj(X_b[k]) for every a <= b;
+ * and at the end of each integration returns V_ab / (W_ab * N), W_ab being
+ * the number of blocks valid at both stations.
+ *
+ * Input format.  One byte stream per station; G = subbands*pols streams are
+ * interleaved per sample time, stream j = subband*pols + pol; the 2-bit code
+ * of stream j at sample-time t (counted from the station's first pushed
+ * sample) sits at bit 2*(t*G + j) of the byte stream, bytes least-significant
+ * bit first.  Default levels: code 0 -> -3.336, 1 -> -1, 2 -> +1, 3 -> +3.336.
+ *
+ * Output layout.  Visibilities are complex64 stored as interleaved float
+ * pairs (re, im) in [baseline][subband][pol][channel] order; baselines run
+ * (0,0),(0,1),...,(0,S-1),(1,1),...,(S-1,S-1), nbl = S(S+1)/2.  Weights are
+ * one double per baseline.
+ *
+ * Times are seconds relative to the scan epoch, in FP64.  Block b covers
+ * geocentric samples [b*N, b*N + N); integration i holds the blocks with
+ * i <= b*N / (fs*tint) < i+1 (fs*tint must be a whole number of samples).
+ *
+ * Errors.  Every entry point returns CORR_OK (0) or a negative code; no
+ * exception crosses the ABI.  Arguments are checked before any device work.
+ * corr_last_error() gives a text for the last failure on a handle (or, with a
+ * NULL handle, for the last failed corr_create on this thread).
+ *
+ * Threads and devices.  A handle is not thread-safe.  It lives on the CUDA
+ * device that was current at corr_create and makes that device current at
+ * every call.  Device work runs on the handle's stream (its own, or the one
+ * given to corr_set_stream).
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct corr_s corr_t;
+
+enum {
+  CORR_OK = 0,
+  CORR_EINVAL = -1,   /* bad argument (nothing was changed)                      */
+  CORR_ENOMEM = -2,   /* device or host allocation failed                         */
+  CORR_EAGAIN = -3,   /* a station has not pushed the samples this integration needs */
+  CORR_ETIMEOUT = -4, /* a device wait did not finish in time                     */
+  CORR_ECUDA = -5,    /* a CUDA call failed (text in corr_last_error)             */
+  CORR_ESTATE = -6,   /* call not allowed in the handle's current state           */
+  CORR_EEND = -7      /* after corr_flush: no station has data for the next integration */
+};
+
+enum { CORR_PREC_FP32 = 0 };
+
+/* Create a correlator for one scan.  stations 1..256, subbands*pols 1..32,
+ * pols 1 or 2, nchan a power of two in 4..8192, tint_s > 0.  *h receives the
+ * handle (NULL on failure).  Allocates host state only; device memory is
+ * allocated at the first corr_correlate* call. */
+int corr_create(corr_t **h, int stations, int subbands, int pols, int nchan, double tint_s);
+
+/* Sample rate per stream (Hz, default 32e6) and the code -> level table
+ * (NULL keeps the current one).  Only before the first correlate call. */
+int corr_set_format(corr_t *h, double fs_hz, const float lut[4]);
+
+/* Sky (LO) frequency of a subband in Hz, used for the fringe rotation
+ * exp(+2 pi i frac(nu0 tau)).  Default 0 (no fringe rotation). */
+int corr_set_sky_freq(corr_t *h, int subband, double nu0_hz);
+
+/* Arithmetic of the X step.  Only CORR_PREC_FP32 is accepted. */
+int corr_set_precision(corr_t *h, int mode);
+
+/* Run device work on this cudaStream_t (NULL: the handle's own stream). */
+int corr_set_stream(corr_t *h, void *cuda_stream);
+
+/* Append a delay-polynomial segment for a station:
+ * tau(t) = sum_{i=0..5} coeffs[i] (t - t0_s)^i seconds, valid from t0_s until
+ * the next segment.  t0_s must increase per station (CORR_EINVAL otherwise);
+ * at most 64 segments per station.  A block whose centre precedes the first
+ * segment is not valid.  The delay polynomials come from the delay model
+ * (paper, Sec. 2); a positive tau means the station receives later. */
+int corr_set_delay_poly(corr_t *h, int station, double t0_s, const double coeffs[6]);
+
+/* Station sample index of the first sample that will be pushed (default 0):
+ * a recording that starts before or after the scan epoch.  Only before the
+ * station's first push or attach. */
+int corr_set_stream_start(corr_t *h, int station, int64_t first_sample);
+
+/* Reserve device room for nbytes of a station's packed samples (optional). */
+int corr_reserve(corr_t *h, int station, size_t nbytes);
+
+/* Append packed bytes (host memory) to a station's stream.  nbytes must be a
+ * multiple of 4.  The bytes are copied to the device before the call returns,
+ * so the caller may reuse the buffer; pinned host memory copies fastest. */
+int corr_push_samples(corr_t *h, int station, const void *bytes, size_t nbytes);
+
+/* Use nbytes of packed samples that already live in device memory of the
+ * handle's device (16-byte aligned, nbytes a multiple of 4) as the station's
+ * whole stream.  The caller keeps ownership and must keep the memory alive
+ * and unchanged until corr_destroy or corr_reset.  No push is allowed for
+ * that station afterwards. */
+int corr_attach_samples_device(corr_t *h, int station, const void *dev_bytes, size_t nbytes);
+
+/* Declare the end of data: integrations that reach past a station's data are
+ * then produced with those blocks marked invalid instead of CORR_EAGAIN. */
+int corr_flush(corr_t *h);
+
+/* Correlate the next integration and copy it to host memory.
+ * out: nbl*subbands*pols*nchan complex64 (2 floats each); weights: nbl doubles
+ * or NULL.  Returns CORR_EAGAIN (nothing consumed) when some station has not
+ * pushed the samples the integration needs and corr_flush was not called,
+ * CORR_EEND after corr_flush when no station has data left.  Blocks until the
+ * device work is done. */
+int corr_correlate(corr_t *h, float *out, double *weights);
+
+/* As corr_correlate, but writes the visibilities to device memory dev_out
+ * (same layout) and, if dev_weights is not NULL, the weights to device
+ * memory; returns once the work is enqueued on the handle's stream. */
+int corr_correlate_device(corr_t *h, float *dev_out, double *dev_weights);
+
+/* Index of the integration the next correlate call produces. */
+int corr_next_integration(const corr_t *h, int64_t *index);
+
+/* Start again from integration 0, keeping data and delay model. */
+int corr_rewind(corr_t *h);
+
+/* Drop all pushed or attached samples and flush state, and rewind; the delay
+ * model, format and stream starts are kept. */
+int corr_reset(corr_t *h);
+
+/* Text of the last error on h (NULL h: last corr_create failure). */
+const char *corr_last_error(const corr_t *h);
+
+/* Free the handle and its device memory (NULL is allowed). */
+void corr_destroy(corr_t *h);
+
+/* ---- inspection of intermediate results (for tests; slow) ---------------- */
+
+/* Delay-block results for blocks [b0, b0+nb) of all stations, each array
+ * [stations][nb]: window start (station sample index), eps (s), tau (s),
+ * validity (0/1) against the data present now.  Any pointer may be NULL. */
+int corr_debug_delays(corr_t *h, int64_t b0, int64_t nb, int64_t *start, double *eps, double *tau,
+                      uint8_t *valid);
+
+/* 2-bit codes of one station's stream for sample-time groups [t0, t0+count)
+ * counted from its first sample, as read on the device (0xFF outside). */
+int corr_debug_codes(corr_t *h, int station, int stream, int64_t t0, int64_t count, uint8_t *codes);
+
+/* The rotated spectrum of one station, stream and block (nchan complex64),
+ * as the F step produces it; *valid receives the block's validity. */
+int corr_debug_spectrum(corr_t *h, int station, int stream, int64_t block, float *out, int *valid);
+
+/* Time every stage launch with CUDA events on the handle's stream (off by
+ * default).  Stages: 0 delay blocks, 1 F (unpack+FFT+rotate), 2 X
+ * (cross-multiply-accumulate), 3 weights+finalise. */
+int corr_set_profiling(corr_t *h, int enable);
+
+/* Wait for the recorded events, return per stage the summed device time
+ * (ms) and the number of launches since the last read, and reset them. */
+int corr_read_profile(corr_t *h, double ms[4], int64_t launches[4]);
+
+/* Blocks per F/X chunk and the number of X partial accumulators the handle
+ * uses (valid after the first correlate call). */
+int corr_launch_shape(const corr_t *h, int *chunk_blocks, int *kz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CORR_H */

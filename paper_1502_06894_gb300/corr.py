@@ -1,0 +1,258 @@
+"""ctypes binding of libcorr.so (include/corr.h).
+
+Argument marshalling only: every step of the correlator runs in the CUDA
+library.  The functions keep the C names; ``Correlator`` wraps a handle.
+There is no CPU fallback: importing this module without a built libcorr.so,
+or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcorr.so")
+
+CORR_OK = 0
+CORR_EINVAL = -1
+CORR_ENOMEM = -2
+CORR_EAGAIN = -3
+CORR_ETIMEOUT = -4
+CORR_ECUDA = -5
+CORR_ESTATE = -6
+CORR_EEND = -7
+CORR_PREC_FP32 = 0
+
+_ERRNAMES = {0: "CORR_OK", -1: "CORR_EINVAL", -2: "CORR_ENOMEM", -3: "CORR_EAGAIN", -4: "CORR_ETIMEOUT",
+             -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libcorr.so is not built (run __graft_entry__.build() or "
+                      "python paper_1502_06894_gb300/_build.py); there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+_P = C.c_void_p
+_H = C.c_void_p
+_SIGS = {
+    "corr_create": ([C.POINTER(_H), C.c_int, C.c_int, C.c_int, C.c_int, C.c_double], C.c_int),
+    "corr_set_format": ([_H, C.c_double, _P], C.c_int),
+    "corr_set_sky_freq": ([_H, C.c_int, C.c_double], C.c_int),
+    "corr_set_precision": ([_H, C.c_int], C.c_int),
+    "corr_set_stream": ([_H, _P], C.c_int),
+    "corr_set_delay_poly": ([_H, C.c_int, C.c_double, _P], C.c_int),
+    "corr_set_stream_start": ([_H, C.c_int, C.c_int64], C.c_int),
+    "corr_reserve": ([_H, C.c_int, C.c_size_t], C.c_int),
+    "corr_push_samples": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
+    "corr_attach_samples_device": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
+    "corr_flush": ([_H], C.c_int),
+    "corr_correlate": ([_H, _P, _P], C.c_int),
+    "corr_correlate_device": ([_H, _P, _P], C.c_int),
+    "corr_next_integration": ([_H, C.POINTER(C.c_int64)], C.c_int),
+    "corr_rewind": ([_H], C.c_int),
+    "corr_reset": ([_H], C.c_int),
+    "corr_last_error": ([_H], C.c_char_p),
+    "corr_destroy": ([_H], None),
+    "corr_debug_delays": ([_H, C.c_int64, C.c_int64, _P, _P, _P, _P], C.c_int),
+    "corr_debug_codes": ([_H, C.c_int, C.c_int, C.c_int64, C.c_int64, _P], C.c_int),
+    "corr_debug_spectrum": ([_H, C.c_int, C.c_int, C.c_int64, _P, C.POINTER(C.c_int)], C.c_int),
+    "corr_set_profiling": ([_H, C.c_int], C.c_int),
+    "corr_read_profile": ([_H, _P, _P], C.c_int),
+    "corr_launch_shape": ([_H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+
+EXPORTED = tuple(_SIGS)
+
+
+class CorrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (_ERRNAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return int(a)
+
+
+class Correlator:
+    """One scan: S stations, nsub subbands x npol pols, nchan channels."""
+
+    def __init__(self, stations: int, subbands: int, pols: int, nchan: int, tint: float,
+                 fs: float = 32e6, lut: Optional[Sequence[float]] = None):
+        h = _H()
+        rc = corr_create(C.byref(h), stations, subbands, pols, nchan, float(tint))
+        if rc != CORR_OK:
+            raise CorrError(rc, corr_last_error(None).decode())
+        self.h = h
+        self.S, self.nsub, self.npol, self.nchan = stations, subbands, pols, nchan
+        self.G = subbands * pols
+        self.nbl = stations * (stations + 1) // 2
+        self._keep = []
+        if fs != 32e6 or lut is not None:
+            lt = None if lut is None else np.asarray(lut, np.float32)
+            self._check(corr_set_format(self.h, float(fs), _ptr(lt)))
+
+    # ---------------------------------------------------------------- utils
+    def _check(self, rc: int) -> int:
+        if rc != CORR_OK:
+            raise CorrError(rc, corr_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            corr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- setup
+    def set_sky_freq(self, subband: int, nu0: float):
+        self._check(corr_set_sky_freq(self.h, subband, float(nu0)))
+
+    def set_stream(self, stream_handle: int):
+        self._check(corr_set_stream(self.h, stream_handle))
+
+    def set_delay_poly(self, station: int, t0: float, coeffs: Sequence[float]):
+        c = np.zeros(6, np.float64)
+        c[:len(coeffs)] = coeffs
+        self._check(corr_set_delay_poly(self.h, station, float(t0), _ptr(c)))
+
+    def set_stream_start(self, station: int, first_sample: int):
+        self._check(corr_set_stream_start(self.h, station, int(first_sample)))
+
+    def reserve(self, station: int, nbytes: int):
+        self._check(corr_reserve(self.h, station, int(nbytes)))
+
+    def push(self, station: int, data):
+        """Append packed bytes (numpy uint8 array or a pinned host torch tensor)."""
+        if isinstance(data, np.ndarray):
+            data = np.ascontiguousarray(data, dtype=np.uint8)
+            n = data.nbytes
+        else:
+            n = data.numel() * data.element_size()
+        self._check(corr_push_samples(self.h, station, _ptr(data), n))
+
+    def attach_device(self, station: int, dev_tensor):
+        """Use a CUDA tensor's bytes as the station's whole stream (kept alive here)."""
+        self._keep.append(dev_tensor)
+        n = dev_tensor.numel() * dev_tensor.element_size()
+        self._check(corr_attach_samples_device(self.h, station, dev_tensor.data_ptr(), n))
+
+    def flush(self):
+        self._check(corr_flush(self.h))
+
+    def rewind(self):
+        self._check(corr_rewind(self.h))
+
+    def reset(self):
+        self._check(corr_reset(self.h))
+        self._keep = []
+
+    # ---------------------------------------------------------------- run
+    def correlate(self, weights: bool = True):
+        """Next integration -> (vis [nbl, nsub, npol, nchan] complex64, weights [nbl])
+        or None when the library answers CORR_EAGAIN / CORR_EEND."""
+        out = np.empty((self.nbl, self.nsub, self.npol, self.nchan), np.complex64)
+        w = np.empty(self.nbl, np.float64) if weights else None
+        rc = corr_correlate(self.h, _ptr(out), _ptr(w))
+        if rc in (CORR_EAGAIN, CORR_EEND):
+            return None
+        self._check(rc)
+        return out, w
+
+    def correlate_into(self, out, weights=None) -> int:
+        """Host-buffer variant that returns the code (no allocation)."""
+        return corr_correlate(self.h, _ptr(out), _ptr(weights))
+
+    def correlate_device(self, dev_out, dev_weights=None) -> int:
+        rc = corr_correlate_device(self.h, _ptr(dev_out), _ptr(dev_weights))
+        if rc not in (CORR_OK, CORR_EAGAIN, CORR_EEND):
+            self._check(rc)
+        return rc
+
+    def next_integration(self) -> int:
+        v = C.c_int64()
+        self._check(corr_next_integration(self.h, C.byref(v)))
+        return v.value
+
+    # ---------------------------------------------------------------- inspection
+    STAGES = ("delay", "fstage", "xstage", "finalize")
+
+    def set_profiling(self, on: bool = True):
+        self._check(corr_set_profiling(self.h, int(on)))
+
+    def read_profile(self):
+        """{stage: (total ms, launches)} since the last read."""
+        ms = np.zeros(4, np.float64)
+        n = np.zeros(4, np.int64)
+        self._check(corr_read_profile(self.h, _ptr(ms), _ptr(n)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.STAGES)}
+
+    def launch_shape(self):
+        cb, kz = C.c_int(), C.c_int()
+        self._check(corr_launch_shape(self.h, C.byref(cb), C.byref(kz)))
+        return cb.value, kz.value
+
+    def debug_delays(self, b0: int, nb: int):
+        start = np.zeros((self.S, nb), np.int64)
+        eps = np.zeros((self.S, nb))
+        tau = np.zeros((self.S, nb))
+        valid = np.zeros((self.S, nb), np.uint8)
+        self._check(corr_debug_delays(self.h, b0, nb, _ptr(start), _ptr(eps), _ptr(tau), _ptr(valid)))
+        return start, eps, tau, valid
+
+    def debug_codes(self, station: int, stream: int, t0: int, count: int):
+        out = np.zeros(count, np.uint8)
+        self._check(corr_debug_codes(self.h, station, stream, t0, count, _ptr(out)))
+        return out
+
+    def debug_spectrum(self, station: int, stream: int, block: int):
+        out = np.zeros(self.nchan, np.complex64)
+        v = C.c_int()
+        self._check(corr_debug_spectrum(self.h, station, stream, block, _ptr(out), C.byref(v)))
+        return out, bool(v.value)
+
+
+def from_scan(scan, streams=None, device_streams=None, nchan=None) -> Correlator:
+    """Configure a Correlator from a synthetic scan description (stations,
+    shapes, sky frequencies, delay segments, stream starts) and optionally
+    push host streams or attach device streams."""
+    c = Correlator(scan.stations, scan.nsub, scan.npol, nchan or scan.nchan, scan.tint, fs=scan.fs)
+    for sb, nu in enumerate(scan.nu0):
+        if nu:
+            c.set_sky_freq(sb, nu)
+    for s, segs in enumerate(scan.polys):
+        for seg in segs:
+            c.set_delay_poly(s, seg.t0, seg.coeffs)
+        c.set_stream_start(s, scan.sample0[s])
+    if streams is not None:
+        for s, b in enumerate(streams):
+            c.push(s, b)
+    if device_streams is not None:
+        for s, t in enumerate(device_streams):
+            c.attach_device(s, t)
+    return c

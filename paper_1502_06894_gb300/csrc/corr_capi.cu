@@ -1,0 +1,832 @@
+// corr_capi.cu -- the handle runtime behind include/corr.h: argument checks,
+// station streams in device memory, the delay model on the device, and the
+// per-integration schedule of kernels (delay blocks -> [F, X] per chunk ->
+// weights -> finalise).
+#include "../../include/corr.h"
+#include "corr_internal.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace corr;
+
+constexpr int kStages = 4;  // delay blocks, F, X, weights+finalise
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Seg {
+  double t0;
+  double c[6];
+};
+
+struct Station {
+  uint8_t* dbuf = nullptr;  // owned device bytes
+  size_t cap = 0;
+  size_t len = 0;           // bytes present
+  const uint8_t* ext = nullptr;  // attached (caller-owned) device bytes
+  bool attached = false;
+  int64_t sample0 = 0;
+  bool started = false;     // a push or attach happened
+  std::vector<Seg> segs;
+};
+
+bool g_const_ready[64];
+std::mutex g_const_mu;
+
+}  // namespace
+
+struct corr_s {
+  int dev = 0;
+  int S = 0, nsub = 0, npol = 0, G = 0, nchan = 0, N = 0;
+  double tint = 0.0, fs = 32e6;
+  int64_t spi = 0;
+  float lut[4] = {-3.336f, -1.0f, 1.0f, 3.336f};
+  std::vector<double> nu0;
+  int precision = CORR_PREC_FP32;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<Station> st;
+  bool flushed = false;
+  int64_t next_int = 0;
+  bool polys_dirty = true;
+  bool prepared = false;
+
+  // device state
+  StationView* d_views = nullptr;
+  StationView* h_views = nullptr;  // pinned staging
+  int* d_nseg = nullptr;
+  double* d_seg_t0 = nullptr;
+  double* d_seg_c = nullptr;
+  double* d_nu0 = nullptr;
+  int Mcap = 0;
+  int64_t* d_start = nullptr;
+  float* d_delta = nullptr;
+  float* d_phi = nullptr;
+  uint8_t* d_valid = nullptr;
+  unsigned long long* d_stat = nullptr;  // [S][3]
+  unsigned long long* h_stat = nullptr;  // pinned
+  float2* d_twN = nullptr;
+  int CB = 0, KZ = 0;
+  float2* d_spec = nullptr;
+  float2* d_part = nullptr;
+  float2* d_out = nullptr;
+  int* d_wcount = nullptr;
+  double* d_wts = nullptr;
+  size_t spec_budget = (size_t)1 << 30;
+
+  // optional per-stage CUDA-event timing of the launches
+  bool profiling = false;
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[kStages] = {0};
+  int64_t prof_n[kStages] = {0};
+
+  std::string err;
+
+  int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CORR_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+};
+
+#define CK(call, what)                                    \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return h->cuda_fail(e_, what); \
+  } while (0)
+
+static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+static int use_device(corr_t* h) {
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->dev) {
+    cudaError_t e = cudaSetDevice(h->dev);
+    if (e != cudaSuccess) return h->cuda_fail(e, "cudaSetDevice");
+  }
+  return CORR_OK;
+}
+
+static cudaEvent_t take_event(corr_t* h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Record an event before (begin) / after (end) a stage's launch when profiling.
+static cudaEvent_t prof_begin(corr_t* h) {
+  if (!h->profiling) return nullptr;
+  cudaEvent_t a = take_event(h);
+  if (a) cudaEventRecord(a, h->stream);
+  return a;
+}
+
+static void prof_end(corr_t* h, int stage, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b = take_event(h);
+  if (!b) {
+    h->ev_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(b, h->stream);
+  h->marks.push_back({stage, a, b});
+}
+
+static int prof_collect(corr_t* h) {
+  for (auto& m : h->marks) {
+    cudaError_t e = cudaEventSynchronize(m.b);
+    if (e != cudaSuccess) return h->cuda_fail(e, "profile event");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m.a, m.b);
+    h->prof_ms[m.stage] += ms;
+    h->prof_n[m.stage] += 1;
+    h->ev_pool.push_back(m.a);
+    h->ev_pool.push_back(m.b);
+  }
+  h->marks.clear();
+  return CORR_OK;
+}
+
+static int64_t station_groups(const corr_t* h, const Station& s) {
+  return (int64_t)((s.len * 4) / (size_t)h->G);
+}
+
+static const uint8_t* station_ptr(const Station& s) { return s.attached ? s.ext : s.dbuf; }
+
+static int64_t integ_first_block(const corr_t* h, int64_t i) {
+  return (i * h->spi + h->N - 1) / h->N;
+}
+
+// ------------------------------------------------------------------------
+// device preparation
+
+static void free_device(corr_t* h) {
+  cudaFree(h->d_views);
+  cudaFreeHost(h->h_views);
+  cudaFree(h->d_nseg);
+  cudaFree(h->d_seg_t0);
+  cudaFree(h->d_seg_c);
+  cudaFree(h->d_nu0);
+  cudaFree(h->d_start);
+  cudaFree(h->d_delta);
+  cudaFree(h->d_phi);
+  cudaFree(h->d_valid);
+  cudaFree(h->d_stat);
+  cudaFreeHost(h->h_stat);
+  cudaFree(h->d_twN);
+  cudaFree(h->d_spec);
+  cudaFree(h->d_part);
+  cudaFree(h->d_out);
+  cudaFree(h->d_wcount);
+  cudaFree(h->d_wts);
+  h->d_wts = nullptr;
+  h->d_views = nullptr; h->h_views = nullptr; h->d_nseg = nullptr; h->d_seg_t0 = nullptr;
+  h->d_seg_c = nullptr; h->d_nu0 = nullptr; h->d_start = nullptr; h->d_delta = nullptr;
+  h->d_phi = nullptr; h->d_valid = nullptr; h->d_stat = nullptr; h->h_stat = nullptr;
+  h->d_twN = nullptr; h->d_spec = nullptr; h->d_part = nullptr; h->d_out = nullptr;
+  h->d_wcount = nullptr;
+  h->prepared = false;
+}
+
+static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return h->fail(CORR_ENOMEM, "cudaMalloc %s (%zu bytes): %s", what, bytes, cudaGetErrorString(e));
+  }
+  return CORR_OK;
+}
+
+static int prepare(corr_t* h) {
+  if (h->prepared) return CORR_OK;
+  {
+    const double spi = h->fs * h->tint;
+    if (fabs(spi - (double)llround(spi)) > 1e-6 || llround(spi) < h->N)
+      return h->fail(CORR_EINVAL, "fs*tint = %.9g must be a whole number of samples >= 2*nchan", spi);
+    h->spi = llround(spi);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    if (h->dev >= 0 && h->dev < 64 && !g_const_ready[h->dev]) {
+      CK(fstage_init_constants(), "fstage constants");
+      g_const_ready[h->dev] = true;
+    }
+  }
+  const int S = h->S, G = h->G, nch = h->nchan, nbl = nbl_of(S);
+  h->Mcap = (int)((h->spi + h->N - 1) / h->N) + 1;
+  const size_t per_block = (size_t)G * S * nch * sizeof(float2);
+  int64_t cb = (int64_t)(h->spec_budget / per_block);
+  if (cb < 1) cb = 1;
+  if (cb > h->Mcap) cb = h->Mcap;
+  h->CB = (int)cb;
+  h->KZ = xstage_kz(h->CB, S, G, nch);
+  int rc;
+  if ((rc = dalloc(h, (void**)&h->d_views, sizeof(StationView) * S, "views"))) return rc;
+  CK(cudaMallocHost((void**)&h->h_views, sizeof(StationView) * S), "cudaMallocHost views");
+  if ((rc = dalloc(h, (void**)&h->d_nseg, sizeof(int) * S, "nseg"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_seg_t0, sizeof(double) * S * kMaxSegs, "seg_t0"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_seg_c, sizeof(double) * S * kMaxSegs * 6, "seg_c"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_nu0, sizeof(double) * h->nsub, "nu0"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_start, sizeof(int64_t) * S * h->Mcap, "start"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_delta, sizeof(float) * S * h->Mcap, "delta"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_phi, sizeof(float) * S * h->nsub * h->Mcap, "phi"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_valid, (size_t)S * h->Mcap, "valid"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_stat, sizeof(unsigned long long) * 3 * S, "stat"))) return rc;
+  CK(cudaMallocHost((void**)&h->h_stat, sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
+  if ((rc = dalloc(h, (void**)&h->d_twN, sizeof(float2) * h->N, "twiddles"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_spec, per_block * h->CB, "spectra"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_part, sizeof(float2) * (size_t)h->KZ * nbl * G * nch, "partials"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_out, sizeof(float2) * (size_t)nbl * G * nch, "out"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_wcount, sizeof(int) * nbl, "wcount"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_wts, sizeof(double) * nbl, "weights"))) return rc;
+  // W_N^m = exp(-2 pi i m / N), computed in FP64 on the host
+  std::vector<float2> tw(h->N);
+  for (int m = 0; m < h->N; ++m) {
+    double a = -2.0 * 3.14159265358979323846 * (double)m / (double)h->N;
+    tw[m] = make_float2((float)cos(a), (float)sin(a));
+  }
+  CK(cudaMemcpy(h->d_twN, tw.data(), sizeof(float2) * h->N, cudaMemcpyHostToDevice), "twiddles H2D");
+  h->prepared = true;
+  h->polys_dirty = true;
+  return CORR_OK;
+}
+
+static int upload_model(corr_t* h) {
+  const int S = h->S;
+  for (int s = 0; s < S; ++s)
+    if (h->st[s].segs.empty()) return h->fail(CORR_EINVAL, "station %d has no delay polynomial", s);
+  if (h->polys_dirty) {
+    std::vector<int> nseg(S);
+    std::vector<double> t0((size_t)S * kMaxSegs, 0.0), c((size_t)S * kMaxSegs * 6, 0.0);
+    for (int s = 0; s < S; ++s) {
+      nseg[s] = (int)h->st[s].segs.size();
+      for (int q = 0; q < nseg[s]; ++q) {
+        t0[(size_t)s * kMaxSegs + q] = h->st[s].segs[q].t0;
+        memcpy(&c[((size_t)s * kMaxSegs + q) * 6], h->st[s].segs[q].c, sizeof(double) * 6);
+      }
+    }
+    CK(cudaMemcpy(h->d_nseg, nseg.data(), sizeof(int) * S, cudaMemcpyHostToDevice), "nseg H2D");
+    CK(cudaMemcpy(h->d_seg_t0, t0.data(), sizeof(double) * t0.size(), cudaMemcpyHostToDevice), "t0 H2D");
+    CK(cudaMemcpy(h->d_seg_c, c.data(), sizeof(double) * c.size(), cudaMemcpyHostToDevice), "coeff H2D");
+    CK(cudaMemcpy(h->d_nu0, h->nu0.data(), sizeof(double) * h->nsub, cudaMemcpyHostToDevice), "nu0 H2D");
+    h->polys_dirty = false;
+  }
+  // station views: small pinned staging copied on the stream
+  CK(cudaStreamSynchronize(h->stream), "sync before view update");
+  for (int s = 0; s < S; ++s) {
+    const Station& x = h->st[s];
+    StationView v;
+    v.words = reinterpret_cast<const uint32_t*>(station_ptr(x));
+    v.nwords = (int64_t)(x.len / 4);
+    v.sample0 = x.sample0;
+    v.ngroups = station_groups(h, x);
+    h->h_views[s] = v;
+  }
+  CK(cudaMemcpyAsync(h->d_views, h->h_views, sizeof(StationView) * S, cudaMemcpyHostToDevice, h->stream),
+     "views H2D");
+  return CORR_OK;
+}
+
+static DelayParams delay_params(corr_t* h, int64_t b0, int nb, int ld) {
+  DelayParams p;
+  p.S = h->S;
+  p.nsub = h->nsub;
+  p.N = h->N;
+  p.fs = h->fs;
+  p.nseg = h->d_nseg;
+  p.seg_t0 = h->d_seg_t0;
+  p.seg_c = h->d_seg_c;
+  p.nu0 = h->d_nu0;
+  p.st = h->d_views;
+  p.b0 = b0;
+  p.nb = nb;
+  p.ld = ld;
+  p.start = h->d_start;
+  p.delta = h->d_delta;
+  p.phi = h->d_phi;
+  p.valid = h->d_valid;
+  p.eps_out = nullptr;
+  p.tau_out = nullptr;
+  p.max_end = nullptr;
+  return p;
+}
+
+static FParams fparams(corr_t* h, int blk0, int cb) {
+  FParams p;
+  p.st = h->d_views;
+  p.start = h->d_start;
+  p.delta = h->d_delta;
+  p.phi = h->d_phi;
+  p.valid = h->d_valid;
+  p.ld = h->Mcap;
+  p.blk0 = blk0;
+  p.CB = cb;
+  p.S = h->S;
+  p.G = h->G;
+  p.npol = h->npol;
+  p.nsub = h->nsub;
+  p.nchan = h->nchan;
+  p.lut0 = h->lut[0];
+  p.lut1 = h->lut[1];
+  p.lut2 = h->lut[2];
+  p.lut3 = h->lut[3];
+  p.twN = h->d_twN;
+  p.out_kind = 0;
+  p.out = h->d_spec;
+  return p;
+}
+
+// The whole schedule of one integration.  On success the visibilities are in
+// vis_out (device, [nbl][G][nchan]) and, if given, the weights in w_out.
+static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
+  int rc;
+  if ((rc = use_device(h))) return rc;
+  if ((rc = prepare(h))) return rc;
+  if ((rc = upload_model(h))) return rc;
+  const int S = h->S;
+  const int64_t i = h->next_int;
+  const int64_t bfirst = integ_first_block(h, i);
+  const int M = (int)(integ_first_block(h, i + 1) - bfirst);
+
+  // 1. delay blocks + data-coverage statistics
+  for (int s = 0; s < S; ++s) {
+    h->h_stat[3 * s + 0] = 0ull;
+    h->h_stat[3 * s + 1] = ~0ull;
+    h->h_stat[3 * s + 2] = 0ull;
+  }
+  CK(cudaMemcpyAsync(h->d_stat, h->h_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyHostToDevice, h->stream),
+     "stat H2D");
+  DelayParams dp = delay_params(h, bfirst, M, h->Mcap);
+  dp.max_end = h->d_stat;
+  cudaEvent_t pa = prof_begin(h);
+  CK(launch_delay_blocks(dp, h->stream), "delay_blocks launch");
+  prof_end(h, 0, pa);
+  CK(cudaMemcpyAsync(h->h_stat, h->d_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyDeviceToHost, h->stream),
+     "stat D2H");
+  CK(cudaStreamSynchronize(h->stream), "delay_blocks");
+  const unsigned long long off = 1ull << 62;
+  bool any_data = false;
+  for (int s = 0; s < S; ++s) {
+    const int64_t need = (int64_t)(h->h_stat[3 * s + 0] - off);
+    const int64_t first = (int64_t)(h->h_stat[3 * s + 1] - off);
+    const int64_t have = station_groups(h, h->st[s]);
+    if (need > have && !h->flushed)
+      return h->fail(CORR_EAGAIN, "station %d: integration %lld needs %lld sample groups, %lld present", s,
+                     (long long)i, (long long)need, (long long)have);
+    if (first + h->N <= have) any_data = true;
+  }
+  if (h->flushed && !any_data) return h->fail(CORR_EEND, "no station has data for integration %lld", (long long)i);
+
+  // 2. F and X per chunk
+  const int nbl = nbl_of(S);
+  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)h->KZ * nbl * h->G * h->nchan, h->stream),
+     "partials memset");
+  for (int c0 = 0; c0 < M; c0 += h->CB) {
+    const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
+    FParams fp = fparams(h, c0, cb);
+    pa = prof_begin(h);
+    CK(launch_fstage(fp, h->stream), "fstage launch");
+    prof_end(h, 1, pa);
+    XParams xp;
+    xp.spec = h->d_spec;
+    xp.CB = cb;
+    xp.S = S;
+    xp.G = h->G;
+    xp.nchan = h->nchan;
+    xp.KZ = h->KZ;
+    xp.part = h->d_part;
+    pa = prof_begin(h);
+    CK(launch_xstage(xp, h->stream), "xstage launch");
+    prof_end(h, 2, pa);
+  }
+  // 3. weights + normalisation
+  FinParams fin;
+  fin.part = h->d_part;
+  fin.KZ = h->KZ;
+  fin.S = S;
+  fin.G = h->G;
+  fin.nchan = h->nchan;
+  fin.N = h->N;
+  fin.valid = h->d_valid;
+  fin.ld = h->Mcap;
+  fin.M = M;
+  fin.wcount = h->d_wcount;
+  fin.out = vis_out;
+  fin.weights = w_out;
+  pa = prof_begin(h);
+  CK(launch_weights(fin, h->stream), "weights launch");
+  CK(launch_finalize(fin, h->stream), "finalize launch");
+  prof_end(h, 3, pa);
+  h->next_int = i + 1;
+  return CORR_OK;
+}
+
+// ------------------------------------------------------------------------
+// C ABI
+
+extern "C" {
+
+int corr_create(corr_t** hp, int stations, int subbands, int pols, int nchan, double tint_s) {
+  if (!hp) {
+    g_create_error = "corr_create: h is NULL";
+    return CORR_EINVAL;
+  }
+  *hp = nullptr;
+  if (stations < 1 || stations > kMaxStations) {
+    g_create_error = "corr_create: stations must be 1..256";
+    return CORR_EINVAL;
+  }
+  if (pols < 1 || pols > 2 || subbands < 1 || subbands * pols > 32 || subbands > kMaxSub) {
+    g_create_error = "corr_create: need pols 1..2 and 1 <= subbands*pols <= 32";
+    return CORR_EINVAL;
+  }
+  if (!is_pow2(nchan) || nchan < 4 || nchan > 8192 || !fstage_supported(nchan)) {
+    g_create_error = "corr_create: nchan must be a power of two in 4..8192";
+    return CORR_EINVAL;
+  }
+  if (!(tint_s > 0.0) || !isfinite(tint_s)) {
+    g_create_error = "corr_create: tint must be > 0";
+    return CORR_EINVAL;
+  }
+  corr_t* h = new (std::nothrow) corr_t();
+  if (!h) {
+    g_create_error = "corr_create: out of host memory";
+    return CORR_ENOMEM;
+  }
+  h->S = stations;
+  h->nsub = subbands;
+  h->npol = pols;
+  h->G = subbands * pols;
+  h->nchan = nchan;
+  h->N = 2 * nchan;
+  h->tint = tint_s;
+  h->spi = llround(h->fs * tint_s);
+  h->nu0.assign(subbands, 0.0);
+  h->st.resize(stations);
+  cudaError_t e = cudaGetDevice(&h->dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("corr_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    delete h;
+    return CORR_ECUDA;
+  }
+  h->stream = h->own_stream;
+  *hp = h;
+  return CORR_OK;
+}
+
+int corr_set_format(corr_t* h, double fs_hz, const float lut[4]) {
+  if (!h) return CORR_EINVAL;
+  if (h->prepared) return h->fail(CORR_ESTATE, "corr_set_format: only before the first correlate");
+  if (!(fs_hz > 0.0) || !isfinite(fs_hz)) return h->fail(CORR_EINVAL, "corr_set_format: fs must be > 0");
+  const double spi = fs_hz * h->tint;
+  const int64_t ispi = llround(spi);
+  if (fabs(spi - (double)ispi) > 1e-6 || ispi < h->N)
+    return h->fail(CORR_EINVAL, "corr_set_format: fs*tint must be a whole number of samples >= 2*nchan");
+  if (lut)
+    for (int q = 0; q < 4; ++q)
+      if (!isfinite(lut[q])) return h->fail(CORR_EINVAL, "corr_set_format: level table must be finite");
+  h->fs = fs_hz;
+  h->spi = ispi;
+  if (lut) memcpy(h->lut, lut, sizeof(h->lut));
+  return CORR_OK;
+}
+
+int corr_set_sky_freq(corr_t* h, int subband, double nu0_hz) {
+  if (!h) return CORR_EINVAL;
+  if (subband < 0 || subband >= h->nsub) return h->fail(CORR_EINVAL, "corr_set_sky_freq: subband out of range");
+  if (!isfinite(nu0_hz)) return h->fail(CORR_EINVAL, "corr_set_sky_freq: frequency must be finite");
+  h->nu0[subband] = nu0_hz;
+  h->polys_dirty = true;
+  return CORR_OK;
+}
+
+int corr_set_precision(corr_t* h, int mode) {
+  if (!h) return CORR_EINVAL;
+  if (mode != CORR_PREC_FP32) return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
+  h->precision = mode;
+  return CORR_OK;
+}
+
+int corr_set_stream(corr_t* h, void* s) {
+  if (!h) return CORR_EINVAL;
+  h->stream = s ? (cudaStream_t)s : h->own_stream;
+  return CORR_OK;
+}
+
+int corr_set_delay_poly(corr_t* h, int station, double t0_s, const double coeffs[6]) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_set_delay_poly: station out of range");
+  if (!coeffs || !isfinite(t0_s)) return h->fail(CORR_EINVAL, "corr_set_delay_poly: bad t0 or coeffs");
+  for (int q = 0; q < 6; ++q)
+    if (!isfinite(coeffs[q])) return h->fail(CORR_EINVAL, "corr_set_delay_poly: coefficients must be finite");
+  Station& s = h->st[station];
+  if (!s.segs.empty() && !(t0_s > s.segs.back().t0))
+    return h->fail(CORR_EINVAL, "corr_set_delay_poly: t0 must increase (station %d)", station);
+  if ((int)s.segs.size() >= kMaxSegs) return h->fail(CORR_EINVAL, "corr_set_delay_poly: at most 64 segments");
+  Seg g;
+  g.t0 = t0_s;
+  memcpy(g.c, coeffs, sizeof(g.c));
+  s.segs.push_back(g);
+  h->polys_dirty = true;
+  return CORR_OK;
+}
+
+int corr_set_stream_start(corr_t* h, int station, int64_t first_sample) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_set_stream_start: station out of range");
+  if (h->st[station].started) return h->fail(CORR_ESTATE, "corr_set_stream_start: station already has data");
+  h->st[station].sample0 = first_sample;
+  return CORR_OK;
+}
+
+static int grow(corr_t* h, Station& s, size_t need) {
+  if (need <= s.cap) return CORR_OK;
+  size_t cap = s.cap ? s.cap : ((size_t)1 << 20);
+  while (cap < need) cap *= 2;
+  uint8_t* nb = nullptr;
+  int rc = dalloc(h, (void**)&nb, cap, "station stream");
+  if (rc) return rc;
+  if (s.len) {
+    cudaError_t e = cudaMemcpyAsync(nb, s.dbuf, s.len, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      cudaFree(nb);
+      return h->cuda_fail(e, "stream grow copy");
+    }
+  }
+  cudaFree(s.dbuf);
+  s.dbuf = nb;
+  s.cap = cap;
+  return CORR_OK;
+}
+
+int corr_reserve(corr_t* h, int station, size_t nbytes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_reserve: station out of range");
+  if (h->st[station].attached) return h->fail(CORR_ESTATE, "corr_reserve: station uses attached memory");
+  int rc = use_device(h);
+  if (rc) return rc;
+  return grow(h, h->st[station], nbytes);
+}
+
+int corr_push_samples(corr_t* h, int station, const void* bytes, size_t nbytes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_push_samples: station out of range");
+  if (nbytes % 4) return h->fail(CORR_EINVAL, "corr_push_samples: nbytes must be a multiple of 4");
+  if (nbytes && !bytes) return h->fail(CORR_EINVAL, "corr_push_samples: bytes is NULL");
+  Station& s = h->st[station];
+  if (s.attached) return h->fail(CORR_ESTATE, "corr_push_samples: station uses attached device memory");
+  if (h->flushed) return h->fail(CORR_ESTATE, "corr_push_samples: after corr_flush");
+  int rc = use_device(h);
+  if (rc) return rc;
+  if ((rc = grow(h, s, s.len + nbytes))) return rc;
+  if (nbytes) {
+    CK(cudaMemcpyAsync(s.dbuf + s.len, bytes, nbytes, cudaMemcpyHostToDevice, h->stream), "push H2D");
+    CK(cudaStreamSynchronize(h->stream), "push sync");
+  }
+  s.len += nbytes;
+  s.started = true;
+  return CORR_OK;
+}
+
+int corr_attach_samples_device(corr_t* h, int station, const void* dev_bytes, size_t nbytes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_attach_samples_device: station out of range");
+  if (nbytes % 4) return h->fail(CORR_EINVAL, "corr_attach_samples_device: nbytes must be a multiple of 4");
+  if (!dev_bytes || ((uintptr_t)dev_bytes & 15))
+    return h->fail(CORR_EINVAL, "corr_attach_samples_device: pointer must be non-NULL and 16-byte aligned");
+  Station& s = h->st[station];
+  if (s.started) return h->fail(CORR_ESTATE, "corr_attach_samples_device: station already has data");
+  int rc = use_device(h);
+  if (rc) return rc;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, dev_bytes);
+  if (e != cudaSuccess || at.type != cudaMemoryTypeDevice || at.device != h->dev) {
+    cudaGetLastError();
+    return h->fail(CORR_EINVAL, "corr_attach_samples_device: not device memory of the handle's device");
+  }
+  cudaFree(s.dbuf);
+  s.dbuf = nullptr;
+  s.cap = 0;
+  s.ext = (const uint8_t*)dev_bytes;
+  s.len = nbytes;
+  s.attached = true;
+  s.started = true;
+  return CORR_OK;
+}
+
+int corr_flush(corr_t* h) {
+  if (!h) return CORR_EINVAL;
+  h->flushed = true;
+  return CORR_OK;
+}
+
+int corr_correlate(corr_t* h, float* out, double* weights) {
+  if (!h) return CORR_EINVAL;
+  if (!out) return h->fail(CORR_EINVAL, "corr_correlate: out is NULL");
+  int rc = use_device(h);
+  if (rc) return rc;
+  if ((rc = prepare(h))) return rc;
+  double* dw = weights ? h->d_wts : nullptr;
+  rc = run_integration(h, h->d_out, dw);
+  if (rc == CORR_OK) {
+    const size_t bytes = sizeof(float2) * (size_t)nbl_of(h->S) * h->G * h->nchan;
+    cudaError_t e = cudaMemcpyAsync(out, h->d_out, bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && dw)
+      e = cudaMemcpyAsync(weights, dw, sizeof(double) * nbl_of(h->S), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = h->cuda_fail(e, "correlate D2H");
+  }
+  return rc;
+}
+
+int corr_correlate_device(corr_t* h, float* dev_out, double* dev_weights) {
+  if (!h) return CORR_EINVAL;
+  if (!dev_out) return h->fail(CORR_EINVAL, "corr_correlate_device: dev_out is NULL");
+  return run_integration(h, reinterpret_cast<float2*>(dev_out), dev_weights);
+}
+
+int corr_next_integration(const corr_t* h, int64_t* index) {
+  if (!h || !index) return CORR_EINVAL;
+  *index = h->next_int;
+  return CORR_OK;
+}
+
+int corr_rewind(corr_t* h) {
+  if (!h) return CORR_EINVAL;
+  h->next_int = 0;
+  return CORR_OK;
+}
+
+int corr_reset(corr_t* h) {
+  if (!h) return CORR_EINVAL;
+  int rc = use_device(h);
+  if (rc) return rc;
+  cudaStreamSynchronize(h->stream);
+  for (Station& s : h->st) {
+    if (s.attached) {
+      s.ext = nullptr;
+      s.attached = false;
+      s.len = 0;
+    } else {
+      s.len = 0;
+    }
+    s.started = false;
+  }
+  h->flushed = false;
+  h->next_int = 0;
+  return CORR_OK;
+}
+
+const char* corr_last_error(const corr_t* h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void corr_destroy(corr_t* h) {
+  if (!h) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->dev) cudaSetDevice(h->dev);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (Station& s : h->st) cudaFree(s.dbuf);
+  for (auto& m : h->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  free_device(h);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (cur != h->dev && cur >= 0) cudaSetDevice(cur);
+  delete h;
+}
+
+// ---- inspection ------------------------------------------------------------
+
+int corr_set_profiling(corr_t* h, int enable) {
+  if (!h) return CORR_EINVAL;
+  h->profiling = enable != 0;
+  return CORR_OK;
+}
+
+int corr_read_profile(corr_t* h, double ms[4], int64_t launches[4]) {
+  if (!h || !ms || !launches) return CORR_EINVAL;
+  int rc = use_device(h);
+  if (rc || (rc = prof_collect(h))) return rc;
+  for (int q = 0; q < kStages; ++q) {
+    ms[q] = h->prof_ms[q];
+    launches[q] = h->prof_n[q];
+    h->prof_ms[q] = 0.0;
+    h->prof_n[q] = 0;
+  }
+  return CORR_OK;
+}
+
+int corr_launch_shape(const corr_t* h, int* chunk_blocks, int* kz) {
+  if (!h || !chunk_blocks || !kz) return CORR_EINVAL;
+  *chunk_blocks = h->CB;
+  *kz = h->KZ;
+  return CORR_OK;
+}
+
+int corr_debug_delays(corr_t* h, int64_t b0, int64_t nb, int64_t* start, double* eps, double* tau,
+                      uint8_t* valid) {
+  if (!h) return CORR_EINVAL;
+  if (nb <= 0 || nb > (1 << 24)) return h->fail(CORR_EINVAL, "corr_debug_delays: nb must be 1..2^24");
+  int rc;
+  if ((rc = use_device(h)) || (rc = prepare(h)) || (rc = upload_model(h))) return rc;
+  const int S = h->S;
+  int64_t* d_start = nullptr;
+  float* d_delta = nullptr;
+  float* d_phi = nullptr;
+  uint8_t* d_valid = nullptr;
+  double *d_eps = nullptr, *d_tau = nullptr;
+  const size_t n = (size_t)S * nb;
+  if ((rc = dalloc(h, (void**)&d_start, n * 8, "dbg")) || (rc = dalloc(h, (void**)&d_delta, n * 4, "dbg")) ||
+      (rc = dalloc(h, (void**)&d_phi, n * 4 * h->nsub, "dbg")) || (rc = dalloc(h, (void**)&d_valid, n, "dbg")) ||
+      (rc = dalloc(h, (void**)&d_eps, n * 8, "dbg")) || (rc = dalloc(h, (void**)&d_tau, n * 8, "dbg"))) {
+    cudaFree(d_start); cudaFree(d_delta); cudaFree(d_phi); cudaFree(d_valid); cudaFree(d_eps); cudaFree(d_tau);
+    return rc;
+  }
+  DelayParams p = delay_params(h, b0, (int)nb, (int)nb);
+  p.start = d_start;
+  p.delta = d_delta;
+  p.phi = d_phi;
+  p.valid = d_valid;
+  p.eps_out = d_eps;
+  p.tau_out = d_tau;
+  cudaError_t e = launch_delay_blocks(p, h->stream);
+  if (e == cudaSuccess && start) e = cudaMemcpyAsync(start, d_start, n * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && eps) e = cudaMemcpyAsync(eps, d_eps, n * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && tau) e = cudaMemcpyAsync(tau, d_tau, n * 8, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && valid) e = cudaMemcpyAsync(valid, d_valid, n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_start); cudaFree(d_delta); cudaFree(d_phi); cudaFree(d_valid); cudaFree(d_eps); cudaFree(d_tau);
+  if (e != cudaSuccess) return h->cuda_fail(e, "corr_debug_delays");
+  return CORR_OK;
+}
+
+int corr_debug_codes(corr_t* h, int station, int stream, int64_t t0, int64_t count, uint8_t* codes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S || stream < 0 || stream >= h->G || count < 0 || !codes)
+    return h->fail(CORR_EINVAL, "corr_debug_codes: bad argument");
+  int rc;
+  if ((rc = use_device(h)) || (rc = prepare(h)) || (rc = upload_model(h))) return rc;
+  uint8_t* d = nullptr;
+  if ((rc = dalloc(h, (void**)&d, (size_t)count, "dbg codes"))) return rc;
+  cudaError_t e = launch_unpack_codes(h->d_views, station, h->G, stream, t0, count, d, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(codes, d, (size_t)count, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return h->cuda_fail(e, "corr_debug_codes");
+  return CORR_OK;
+}
+
+int corr_debug_spectrum(corr_t* h, int station, int stream, int64_t block, float* out, int* valid) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S || stream < 0 || stream >= h->G || !out)
+    return h->fail(CORR_EINVAL, "corr_debug_spectrum: bad argument");
+  int rc;
+  if ((rc = use_device(h)) || (rc = prepare(h)) || (rc = upload_model(h))) return rc;
+  // one-block pass through the same kernels, in the handle's work buffers
+  DelayParams dp = delay_params(h, block, 1, h->Mcap);
+  CK(launch_delay_blocks(dp, h->stream), "delay_blocks");
+  FParams fp = fparams(h, 0, 1);
+  CK(launch_fstage(fp, h->stream), "fstage");
+  const float2* src = h->d_spec + ((size_t)stream * 1 * h->S + station) * h->nchan;
+  CK(cudaMemcpyAsync(out, src, sizeof(float2) * h->nchan, cudaMemcpyDeviceToHost, h->stream), "spectrum D2H");
+  uint8_t v = 0;
+  CK(cudaMemcpyAsync(&v, h->d_valid + (size_t)station * h->Mcap, 1, cudaMemcpyDeviceToHost, h->stream), "valid");
+  CK(cudaStreamSynchronize(h->stream), "corr_debug_spectrum");
+  if (valid) *valid = v;
+  return CORR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// corr_internal.cuh -- shared declarations of the CUDA library (not part of
+// the public C ABI).  Kernels: delay blocks (FP64 delay model), the F stage
+// (unpack + FFT + rotation), the X stage (cross-multiply-accumulate) and the
+// finalisation (weights, normalisation).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace corr {
+
+// Per-station input stream as seen by the kernels: packed 2-bit samples in
+// 32-bit little-endian words; word 0 bit 0 holds stream 0 of station sample
+// `sample0`.
+struct StationView {
+  const uint32_t* words;
+  int64_t nwords;    // whole words present
+  int64_t sample0;   // station sample index of the first sample-time group
+  int64_t ngroups;   // sample-time groups present (for validity)
+};
+
+constexpr int kMaxStations = 256;
+constexpr int kMaxSegs = 64;
+constexpr int kMaxSub = 64;
+
+// Delay-model inputs for the delay-block kernel.
+struct DelayParams {
+  int S, nsub, N;
+  double fs;
+  const int* nseg;          // [S]
+  const double* seg_t0;     // [S][kMaxSegs]
+  const double* seg_c;      // [S][kMaxSegs][6]
+  const double* nu0;        // [nsub]
+  const StationView* st;    // [S]
+  int64_t b0;               // first (absolute) block
+  int nb;                   // blocks
+  int ld;                   // leading dimension of the outputs (>= nb)
+  // outputs, [S][ld] (phi: [S][nsub][ld])
+  int64_t* start;           // absolute station sample of the window start
+  float* delta;             // eps*fs/N: fractional-delay phase slope, turns per channel
+  float* phi;               // frac(nu0*tau), turns
+  uint8_t* valid;
+  double* eps_out;          // optional (debug): eps in seconds
+  double* tau_out;          // optional (debug): tau in seconds
+  unsigned long long* max_end;   // optional [S]: max(window end - sample0) over blocks, encoded +2^62
+};
+
+// F stage: unpack + real FFT + rotation for CB blocks x S stations x G streams.
+struct FParams {
+  const StationView* st;    // [S]
+  const int64_t* start;     // [S][ld]
+  const float* delta;       // [S][ld]
+  const float* phi;         // [S][nsub][ld]
+  const uint8_t* valid;     // [S][ld]
+  int ld;
+  int blk0;                 // first block of the chunk (index into descriptor arrays)
+  int CB;                   // blocks in chunk
+  int S, G, npol, nsub, nchan;
+  float lut0, lut1, lut2, lut3;
+  const float2* twN;        // W_N^m, m < N
+  int out_kind;             // 0: complex FP32 spectra
+  void* out;                // [G][CB][S][nchan]
+};
+
+// X stage: V_ab[k] += X_a[k] conj(X_b[k]) over the chunk's blocks.
+struct XParams {
+  const float2* spec;       // [G][CB][S][nchan]
+  int CB, S, G, nchan;
+  int KZ;                   // block splits per chunk (one partial each)
+  float2* part;             // [KZ][nbl][G][nchan]
+};
+
+struct FinParams {
+  const float2* part;       // [KZ][nbl][G][nchan]
+  int KZ, S, G, nchan, N;
+  const uint8_t* valid;     // [S][ld]
+  int ld, M;                // blocks of the integration
+  int* wcount;              // [nbl] scratch
+  float2* out;              // [nbl][G][nchan]
+  double* weights;          // [nbl] (device, may be null)
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_delay_blocks(const DelayParams& p, cudaStream_t s);
+cudaError_t launch_unpack_codes(const StationView* st_dev, int station, int G, int j, int64_t t0,
+                                int64_t count, uint8_t* out, cudaStream_t s);
+cudaError_t fstage_init_constants();
+bool fstage_supported(int nchan);
+cudaError_t launch_fstage(const FParams& p, cudaStream_t s);
+int xstage_kz(int CB, int S, int G, int nchan);
+cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
+cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
+cudaError_t launch_finalize(const FinParams& p, cudaStream_t s);
+
+__host__ __device__ inline int nbl_of(int S) { return S * (S + 1) / 2; }
+__host__ __device__ inline int bl_index(int a, int b, int S) { return a * S - a * (a - 1) / 2 + (b - a); }
+
+}  // namespace corr

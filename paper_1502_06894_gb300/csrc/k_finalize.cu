@@ -1,0 +1,67 @@
+// k_finalize.cu -- integration end: baseline weights and normalisation.
+//
+// W_ab counts the FFT blocks of the integration that are valid at both
+// stations a and b; blocks valid at only one end were stored as zero spectra
+// and so add nothing to V_ab.  The output is V_ab / (W_ab * N) (zero when
+// W_ab = 0), which puts the autocorrelation of 2-bit data at the mean power of
+// the quantised levels.  The KZ partial accumulators are summed in a fixed
+// order.
+#include "corr_internal.cuh"
+
+namespace corr {
+
+__global__ void k_weights(FinParams p) {
+  const int bl = blockIdx.x;
+  // decode baseline index -> (a, b)
+  int a = 0, q = bl;
+  while (q >= p.S - a) { q -= p.S - a; ++a; }
+  const int b = a + q;
+  const uint8_t* va = p.valid + (size_t)a * p.ld;
+  const uint8_t* vb = p.valid + (size_t)b * p.ld;
+  int cnt = 0;
+  for (int i = threadIdx.x; i < p.M; i += blockDim.x) cnt += (va[i] && vb[i]) ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+  __shared__ int ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += ws[w];
+    p.wcount[bl] = tot;
+    if (p.weights) p.weights[bl] = (double)tot;
+  }
+}
+
+cudaError_t launch_weights(const FinParams& p, cudaStream_t s) {
+  k_weights<<<nbl_of(p.S), 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void k_finalize(FinParams p) {
+  const size_t per = (size_t)p.G * p.nchan;
+  const size_t total = (size_t)nbl_of(p.S) * per;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int bl = (int)(e / per);
+    float2 v = make_float2(0.f, 0.f);
+    for (int kz = 0; kz < p.KZ; ++kz) {
+      const float2 x = p.part[(size_t)kz * total + e];
+      v.x += x.x;
+      v.y += x.y;
+    }
+    const int w = p.wcount[bl];
+    const float sc = w > 0 ? (float)(1.0 / ((double)w * (double)p.N)) : 0.f;
+    p.out[e] = make_float2(v.x * sc, v.y * sc);
+  }
+}
+
+cudaError_t launch_finalize(const FinParams& p, cudaStream_t s) {
+  const size_t total = (size_t)nbl_of(p.S) * p.G * p.nchan;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_finalize<<<blocks, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace corr

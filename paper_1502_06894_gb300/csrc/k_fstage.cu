@@ -1,0 +1,338 @@
+// k_fstage.cu -- the F step of the FX correlator (the paper, Abstract: each
+// station's samples are Fourier transformed first, then cross-multiplied).
+//
+// One CTA takes one station and a few FFT blocks.  Per block it stages the
+// packed 2-bit words of the delay-tracked window [b*N + n_b, +N) in shared
+// memory once (all G streams of a station share one window), then each
+// FFT group of T threads transforms one stream:
+//
+//   unpack   2-bit code -> level (4-entry table), two real samples per complex
+//            point, decoded straight into the registers of the first pass;
+//   FFT      N real samples as an N/2-point complex FFT (even samples in the
+//            real part, odd in the imaginary part), Stockham auto-sort passes
+//            of radix 8/16/32 held in registers, shared memory between passes
+//            (Stockham formulation as in Govindaraju et al., SC08);
+//   split    X[k] = E[k] + W_N^k O[k], E = (Z[k] + conj Z[L-k])/2,
+//            O = (Z[k] - conj Z[L-k])/(2i), k = 0..N/2-1 (Nyquist dropped);
+//   rotate   X[k] *= exp(+2 pi i (phi + k*delta)), phi = frac(nu0 tau) and
+//            delta = eps*fs/N from the FP64 delay kernel, FP32 within the block;
+//   store    complex FP32 spectra [stream][block][station][channel].
+//
+// Blocks that are not valid at this station (window outside the data, or no
+// delay segment yet) store zeros, so they add nothing in the X step.
+#include "corr_internal.cuh"
+
+#include <math.h>
+
+namespace corr {
+
+__constant__ float2 c_w32[32];  // exp(-2 pi i m / 32)
+
+cudaError_t fstage_init_constants() {
+  float2 h[32];
+  for (int m = 0; m < 32; ++m) {
+    double a = -2.0 * 3.14159265358979323846 * (double)m / 32.0;
+    h[m] = make_float2((float)cos(a), (float)sin(a));
+  }
+  return cudaMemcpyToSymbol(c_w32, h, sizeof(h));
+}
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+__host__ __device__ constexpr int bitrevc(int x, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+  return r;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+// In-register DFT of R points (R <= 32): radix-2 decimation in frequency,
+// natural-order input, output permuted back to natural order.
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  constexpr int LOG = ilog2c(R);
+#pragma unroll
+  for (int st = 0; st < LOG; ++st) {
+    const int half = R >> (st + 1);
+#pragma unroll
+    for (int i = 0; i < R; i += 2 * half) {
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float2 a = v[i + k], b = v[i + k + half];
+        v[i + k] = make_float2(a.x + b.x, a.y + b.y);
+        const float2 d = make_float2(a.x - b.x, a.y - b.y);
+        const int m = k * (32 / (2 * half));  // W_{2 half}^k = W_32^m
+        if (m == 0)
+          v[i + k + half] = d;
+        else if (m == 8)
+          v[i + k + half] = make_float2(d.y, -d.x);
+        else
+          v[i + k + half] = cmul(d, c_w32[m]);
+      }
+    }
+  }
+  float2 t[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) t[r] = v[bitrevc(r, LOG)];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = t[r];
+}
+
+template <int T>
+__device__ __forceinline__ void gsync(int grp) {
+  if constexpr (T <= 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(T) : "memory");
+  }
+}
+
+__device__ __forceinline__ float level(uint32_t c, float l0, float l1, float l2, float l3) {
+  const float lo = (c & 1u) ? l1 : l0;
+  const float hi = (c & 1u) ? l3 : l2;
+  return (c & 2u) ? hi : lo;
+}
+
+// A later Stockham pass: read R points per butterfly group, twiddle, DFT,
+// write back in place (all reads of the group finish before any write).
+template <int L, int R, int NS, int T>
+__device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, int grp,
+                                              const float2* __restrict__ twN) {
+  constexpr int GROUPS = L / R;
+  constexpr int PER = GROUPS / T;
+  static_assert(PER >= 1 && GROUPS % T == 0, "bad FFT plan");
+  float2 v[PER][R];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int j = t + u * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[u][r] = buf[pad32(j + r * GROUPS)];
+  }
+  gsync<T>(grp);
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int j = t + u * T;
+    const int k = j & (NS - 1);
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{2 k r L/(NS R)}
+      const float2 w = __ldg(&twN[2 * k * r * (L / (NS * R))]);
+      v[u][r] = cmul(v[u][r], w);
+    }
+    dft_reg<R>(v[u]);
+    const int idxD = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad32(idxD + r * NS)] = v[u][r];
+  }
+  gsync<T>(grp);
+}
+
+// FFT plans: L = N/2 complex points; radices R0*R1*R2 = L; T threads per FFT.
+template <int L> struct Plan;
+template <> struct Plan<4>    { static constexpr int R0 = 4,  R1 = 1,  R2 = 1, T = 1; };
+template <> struct Plan<8>    { static constexpr int R0 = 8,  R1 = 1,  R2 = 1, T = 1; };
+template <> struct Plan<16>   { static constexpr int R0 = 16, R1 = 1,  R2 = 1, T = 1; };
+template <> struct Plan<32>   { static constexpr int R0 = 32, R1 = 1,  R2 = 1, T = 1; };
+template <> struct Plan<64>   { static constexpr int R0 = 8,  R1 = 8,  R2 = 1, T = 8; };
+template <> struct Plan<128>  { static constexpr int R0 = 16, R1 = 8,  R2 = 1, T = 8; };
+template <> struct Plan<256>  { static constexpr int R0 = 16, R1 = 16, R2 = 1, T = 16; };
+template <> struct Plan<512>  { static constexpr int R0 = 32, R1 = 16, R2 = 1, T = 16; };
+template <> struct Plan<1024> { static constexpr int R0 = 32, R1 = 32, R2 = 1, T = 32; };
+template <> struct Plan<2048> { static constexpr int R0 = 16, R1 = 16, R2 = 8, T = 128; };
+template <> struct Plan<4096> { static constexpr int R0 = 16, R1 = 16, R2 = 16, T = 256; };
+template <> struct Plan<8192> { static constexpr int R0 = 32, R1 = 16, R2 = 16, T = 256; };
+
+template <int L> struct Groups {
+  static constexpr int T = Plan<L>::T;
+  static constexpr int NGRP = T == 1 ? 64 : (T >= 128 ? (256 / T) : 256 / T);
+};
+
+constexpr int kBufPad(int L) { return L + L / 32 + 1; }
+
+__host__ __device__ inline int wslot_words(int N, int G) {
+  // window bits 2*N*G plus up to 31 bits of misalignment, plus one spare word
+  return (((2 * N * G + 31 + 31) >> 5) + 1 + 3) & ~3;
+}
+
+template <int L>
+__global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP)
+k_fstage(FParams p, int slots, int wslot) {
+  using P = Plan<L>;
+  constexpr int T = P::T;
+  constexpr int NGRP = Groups<L>::NGRP;
+  constexpr int N = 2 * L;
+  constexpr int BUF = kBufPad(L);
+  constexpr int R0 = P::R0;
+  constexpr int PER0 = L / R0 / T;
+  static_assert(PER0 >= 1, "plan");
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(fbuf_all + NGRP * BUF);
+
+  const int tid = threadIdx.x;
+  const int grp = tid / T;
+  const int t = tid - grp * T;
+  float2* fbuf = fbuf_all + grp * BUF;
+  const int s = blockIdx.y;
+  const int G = p.G;
+  const StationView sv = p.st[s];
+
+  const int bb0 = blockIdx.x * slots;
+  const int nslots = min(slots, p.CB - bb0);
+  if (nslots <= 0) return;
+
+  __shared__ int s_boff[64];
+  __shared__ int s_ok[64];
+
+  // ---- stage the windows of this CTA's blocks ----
+  for (int sl = 0; sl < nslots; ++sl) {
+    const int d = p.blk0 + bb0 + sl;
+    const bool ok = p.valid[(size_t)s * p.ld + d] != 0;
+    int64_t w0 = 0;
+    int boff = 0, nw = 0;
+    if (ok) {
+      const int64_t rel = p.start[(size_t)s * p.ld + d] - sv.sample0;
+      const int64_t bit0 = 2 * rel * G;
+      w0 = bit0 >> 5;
+      boff = (int)(bit0 & 31);
+      nw = (boff + 2 * N * G + 31) >> 5;
+      if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);  // last word may be absent when it holds no window bit
+    }
+    if (tid == 0) {
+      s_boff[sl] = boff;
+      s_ok[sl] = ok ? 1 : 0;
+    }
+    uint32_t* dst = wbuf + sl * wslot;
+    for (int q = tid; q < nw; q += blockDim.x) dst[q] = __ldg(&sv.words[w0 + q]);
+  }
+  __syncthreads();
+
+  const float l0 = p.lut0, l1 = p.lut1, l2 = p.lut2, l3 = p.lut3;
+  const int ntasks = nslots * G;
+  for (int base = 0; base < ntasks; base += NGRP) {
+    const int task = base + grp;
+    const bool active = task < ntasks;
+    const int sl = active ? task / G : 0;
+    const int j = active ? task - sl * G : 0;
+    const bool ok = active && s_ok[sl];
+    const uint32_t* wsl = wbuf + sl * wslot;
+    const int boff = s_boff[sl];
+
+    // ---- pass 0: unpack straight into registers (NS = 1, no twiddles) ----
+    {
+      float2 v[PER0][R0];
+#pragma unroll
+      for (int u = 0; u < PER0; ++u) {
+        const int jj = t + u * T;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int m = jj + r * (L / R0);
+          float x0 = 0.f, x1 = 0.f;
+          if (ok) {
+            const int bit = boff + 2 * (2 * m * G + j);
+            const uint32_t c0 = (wsl[bit >> 5] >> (bit & 31)) & 3u;
+            const int bit1 = bit + 2 * G;
+            const uint32_t c1 = (wsl[bit1 >> 5] >> (bit1 & 31)) & 3u;
+            x0 = level(c0, l0, l1, l2, l3);
+            x1 = level(c1, l0, l1, l2, l3);
+          }
+          v[u][r] = make_float2(x0, x1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PER0; ++u) {
+        const int jj = t + u * T;
+        dft_reg<R0>(v[u]);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) fbuf[pad32(jj * R0 + r)] = v[u][r];
+      }
+      gsync<T>(grp);
+    }
+    if constexpr (P::R1 > 1) stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN);
+    if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
+
+    // ---- real split, rotation, store ----
+    if (active) {
+      const int d = p.blk0 + bb0 + sl;
+      const int bb = bb0 + sl;
+      const float delta = p.delta[(size_t)s * p.ld + d];
+      const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
+      float2* out = reinterpret_cast<float2*>(p.out) + (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
+#pragma unroll 4
+      for (int q = 0; q < L / T; ++q) {
+        const int k = t + q * T;
+        float2 X = make_float2(0.f, 0.f);
+        if (ok) {
+          const float2 Zk = fbuf[pad32(k)];
+          const float2 Zm = fbuf[pad32((L - k) & (L - 1))];
+          // E = (Zk + conj Zm)/2 ; O = (Zk - conj Zm)/(2i)
+          const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+          const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+          const float2 w = __ldg(&p.twN[k]);
+          X = make_float2(E.x + (w.x * O.x - w.y * O.y), E.y + (w.x * O.y + w.y * O.x));
+          float ph = fmaf((float)k, delta, phi);
+          ph -= rintf(ph);
+          float sn, cs;
+          sincospif(2.0f * ph, &sn, &cs);
+          X = make_float2(X.x * cs - X.y * sn, X.x * sn + X.y * cs);
+        }
+        out[k] = X;
+      }
+    }
+    gsync<T>(grp);
+  }
+}
+
+template <int L>
+static cudaError_t launch_L(const FParams& p, cudaStream_t st) {
+  constexpr int T = Plan<L>::T;
+  constexpr int NGRP = Groups<L>::NGRP;
+  const int N = 2 * L;
+  int slots = NGRP / p.G;
+  if (slots < 1) slots = 1;
+  if (slots > 64) slots = 64;
+  const int wslot = wslot_words(N, p.G);
+  const size_t smem = (size_t)NGRP * kBufPad(L) * sizeof(float2) + (size_t)slots * wslot * sizeof(uint32_t);
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(k_fstage<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.CB + slots - 1) / slots, p.S);
+  k_fstage<L><<<grid, T * NGRP, smem, st>>>(p, slots, wslot);
+  return cudaGetLastError();
+}
+
+bool fstage_supported(int nchan) {
+  switch (nchan) {
+    case 4: case 8: case 16: case 32: case 64: case 128: case 256: case 512:
+    case 1024: case 2048: case 4096: case 8192:
+      return true;
+    default:
+      return false;
+  }
+}
+
+cudaError_t launch_fstage(const FParams& p, cudaStream_t s) {
+  if (p.CB <= 0) return cudaSuccess;
+  switch (p.nchan) {
+    case 4: return launch_L<4>(p, s);
+    case 8: return launch_L<8>(p, s);
+    case 16: return launch_L<16>(p, s);
+    case 32: return launch_L<32>(p, s);
+    case 64: return launch_L<64>(p, s);
+    case 128: return launch_L<128>(p, s);
+    case 256: return launch_L<256>(p, s);
+    case 512: return launch_L<512>(p, s);
+    case 1024: return launch_L<1024>(p, s);
+    case 2048: return launch_L<2048>(p, s);
+    case 4096: return launch_L<4096>(p, s);
+    case 8192: return launch_L<8192>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace corr

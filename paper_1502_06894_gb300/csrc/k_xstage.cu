@@ -1,0 +1,137 @@
+// k_xstage.cu -- the X step of the FX correlator on CUDA cores in FP32 (the
+// paper, Abstract: after the Fourier transform every station pair is
+// cross-multiplied).  For each stream g and channel k, over the FFT blocks of
+// a chunk:  V_ab[k] += X_a[k] conj(X_b[k]) for every baseline a <= b
+// (autocorrelations included, parallel hands only).
+//
+// One thread owns one channel of one stream and a TA x TA tile of baselines
+// (a diagonal tile keeps only a <= b), so each loaded spectrum value is used
+// TA times from registers.  The blocks of a chunk are split into KZ ranges;
+// each range sums at most 256 blocks in registers and then adds that partial
+// into its own FP32 accumulator slice part[kz], in a fixed order, so results
+// are deterministic and the FP32 sums stay short (hierarchical accumulation).
+#include "corr_internal.cuh"
+
+namespace corr {
+
+constexpr int kXT = 128;  // threads per CTA (channels)
+
+template <int TA, bool DIAG>
+__global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
+  const int k = blockIdx.x * kXT + threadIdx.x;
+  const int g = blockIdx.y;
+  const int npairs = ntile * (ntile + 1) / 2;
+  const int pair = blockIdx.z % npairs;
+  const int kz = blockIdx.z / npairs;
+  int ta = 0, tb = 0;
+  {
+    int q = pair;
+    while (q >= ntile - ta) { q -= ntile - ta; ++ta; }
+    tb = ta + q;
+  }
+  if (DIAG != (ta == tb)) return;
+  if (k >= p.nchan) return;
+  const int S = p.S;
+  const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
+  const int b_hi = (int)((int64_t)p.CB * (kz + 1) / p.KZ);
+  if (b_hi <= b_lo) return;
+
+  float2 acc[TA][TA];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  const size_t sstride = (size_t)p.nchan;
+  for (int bb = b_lo; bb < b_hi; ++bb) {
+    const float2* base = p.spec + ((size_t)g * p.CB + bb) * (size_t)S * sstride + k;
+    float2 a[TA], b[TA];
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {
+      const int sa = ta * TA + i;
+      a[i] = sa < S ? __ldg(base + sa * sstride) : make_float2(0.f, 0.f);
+    }
+    if (!DIAG) {
+#pragma unroll
+      for (int i = 0; i < TA; ++i) {
+        const int sb = tb * TA + i;
+        b[i] = sb < S ? __ldg(base + sb * sstride) : make_float2(0.f, 0.f);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int j = DIAG ? i : 0; j < TA; ++j) {
+        const float2 y = DIAG ? a[j] : b[j];
+        // X_a conj(X_b)
+        acc[i][j].x = fmaf(a[i].x, y.x, fmaf(a[i].y, y.y, acc[i][j].x));
+        acc[i][j].y = fmaf(a[i].y, y.x, fmaf(-a[i].x, y.y, acc[i][j].y));
+      }
+  }
+  const int nbl = nbl_of(S);
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = DIAG ? i : 0; j < TA; ++j) {
+      const int sa = ta * TA + i, sb = tb * TA + j;
+      if (sa < S && sb < S) {
+        float2* dst = p.part + (((size_t)kz * nbl + bl_index(sa, sb, S)) * p.G + g) * sstride + k;
+        float2 v = *dst;
+        v.x += acc[i][j].x;
+        v.y += acc[i][j].y;
+        *dst = v;
+      }
+    }
+}
+
+static int tile_for(int S) {
+  if (S <= 2) return 2;
+  if (S <= 4) return 4;
+  if (S <= 6) return 6;
+  if (S <= 8) return 8;
+  if (S <= 10) return 10;
+  if (S <= 12) return 12;
+  return 8;
+}
+
+int xstage_kz(int CB, int S, int G, int nchan) {
+  const int TA = tile_for(S);
+  const int nt = (S + TA - 1) / TA;
+  const long ctas = (long)((nchan + kXT - 1) / kXT) * G * (nt * (nt + 1) / 2);
+  int kz = (int)((4L * 152 + ctas - 1) / ctas);  // at least ~4 CTAs per SM
+  const int by256 = (CB + 255) / 256;            // each partial sums <= 256 blocks
+  if (kz < by256) kz = by256;
+  if (kz > CB) kz = CB;
+  if (kz < 1) kz = 1;
+  return kz;
+}
+
+template <int TA>
+static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
+  const int nt = (p.S + TA - 1) / TA;
+  const int npairs = nt * (nt + 1) / 2;
+  dim3 grid((p.nchan + kXT - 1) / kXT, p.G, npairs * p.KZ);
+  k_xmac<TA, true><<<grid, kXT, 0, s>>>(p, nt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || nt == 1) return e;
+  if constexpr (TA == 8) {  // only the 8-station tiling has off-diagonal tiles
+    k_xmac<TA, false><<<grid, kXT, 0, s>>>(p, nt);
+    return cudaGetLastError();
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_xstage(const XParams& p, cudaStream_t s) {
+  if (p.CB <= 0) return cudaSuccess;
+  switch (tile_for(p.S)) {
+    case 2: return launch_TA<2>(p, s);
+    case 4: return launch_TA<4>(p, s);
+    case 6: return launch_TA<6>(p, s);
+    case 8: return launch_TA<8>(p, s);
+    case 10: return launch_TA<10>(p, s);
+    case 12: return launch_TA<12>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace corr
