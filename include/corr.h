@@ -66,7 +66,8 @@ enum {
   CORR_ETIMEOUT = -4, /* a device wait did not finish in time                     */
   CORR_ECUDA = -5,    /* a CUDA call failed (text in corr_last_error)             */
   CORR_ESTATE = -6,   /* call not allowed in the handle's current state           */
-  CORR_EEND = -7      /* after corr_flush: no station has data for the next integration */
+  CORR_EEND = -7,     /* after corr_flush: no station has data for the next integration */
+  CORR_ETOOBIG = -8   /* corr_correlate_static: the shape needs more than its fixed scratch */
 };
 
 enum { CORR_PREC_FP32 = 0 };
@@ -180,6 +181,56 @@ int corr_read_profile(corr_t *h, double ms[4], int64_t launches[4]);
 /* Blocks per F/X chunk and the number of X partial accumulators the handle
  * uses (valid after the first correlate call). */
 int corr_launch_shape(const corr_t *h, int *chunk_blocks, int *kz);
+
+/* ---- correlation without device allocation -------------------------------
+ *
+ * The paper has no counterpart of this entry point; it exists for callers of
+ * this library that cannot let it call cudaMalloc: a host program that owns a
+ * fixed device-memory budget and forbids libraries to allocate after start-up,
+ * or a real-time pipeline that must keep cudaMalloc/cudaFree (which can
+ * synchronise the whole device) off its hot path.
+ *
+ * corr_correlate_static computes integration `integration` of a scan whose
+ * packed samples already live in device memory, exactly as the handle path
+ * does after corr_flush (blocks outside a station's data are not valid), and
+ * writes visibilities to dev_out ([nbl][subbands][pols][nchan] complex64,
+ * device memory) and, unless NULL, the weights to dev_weights (nbl doubles,
+ * device memory).  The caller owns inputs and outputs.  The library allocates
+ * nothing: its intermediates live in one static device array of 64 MiB that
+ * every GPU loading the library holds until the process exits.  A shape whose
+ * intermediates do not fit even with one FFT block per chunk (roughly:
+ * stations x (8*subbands + 13) bytes per block of the integration plus
+ * 8*nbl*subbands*pols*nchan bytes) is rejected with CORR_ETOOBIG.
+ *
+ * The first call on a device resolves the array's device address and loads
+ * the FFT constants for that device (no allocation); make that first call
+ * before any stream capture.  The work is only enqueued on cuda_stream (NULL:
+ * the legacy default stream) when the call returns.  All calls share the one
+ * array, which keeps the last call's contents (the partial sums are cleared
+ * at the start of every call): calls whose device work overlaps -- on two
+ * streams, or from two threads -- race and give wrong results.  Errors are
+ * reported by return code only.
+ *
+ * Descriptor arrays are host memory: nu0_hz[subbands], nseg[stations] (1..64),
+ * seg_t0[stations][64], seg_coeffs[stations][64][6] (delay segments as for
+ * corr_set_delay_poly, unused rows ignored), and per station a device pointer
+ * (16-byte aligned), its byte count (a multiple of 4) and its first station
+ * sample index. */
+typedef struct {
+  int stations, subbands, pols, nchan;
+  double fs_hz, tint_s;
+  float lut[4];
+  const double *nu0_hz;
+  const int *nseg;
+  const double *seg_t0;
+  const double *seg_coeffs;
+  const void *const *dev_bytes;
+  const size_t *nbytes;
+  const int64_t *first_sample;
+} corr_scan_desc;
+
+int corr_correlate_static(const corr_scan_desc *desc, int64_t integration, float *dev_out,
+                          double *dev_weights, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -24,16 +24,26 @@ CORR_ETIMEOUT = -4
 CORR_ECUDA = -5
 CORR_ESTATE = -6
 CORR_EEND = -7
+CORR_ETOOBIG = -8
 CORR_PREC_FP32 = 0
 
 _ERRNAMES = {0: "CORR_OK", -1: "CORR_EINVAL", -2: "CORR_ENOMEM", -3: "CORR_EAGAIN", -4: "CORR_ETIMEOUT",
-             -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND"}
+             -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND", -8: "CORR_ETOOBIG"}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError("libcorr.so is not built (run __graft_entry__.build() or "
                       "python paper_1502_06894_gb300/_build.py); there is no CPU fallback")
 
 _lib = C.CDLL(LIB_PATH)
+
+
+class CorrScanDesc(C.Structure):
+    """corr_scan_desc of include/corr.h."""
+    _fields_ = [("stations", C.c_int), ("subbands", C.c_int), ("pols", C.c_int), ("nchan", C.c_int),
+                ("fs_hz", C.c_double), ("tint_s", C.c_double), ("lut", C.c_float * 4),
+                ("nu0_hz", C.c_void_p), ("nseg", C.c_void_p), ("seg_t0", C.c_void_p),
+                ("seg_coeffs", C.c_void_p), ("dev_bytes", C.c_void_p), ("nbytes", C.c_void_p),
+                ("first_sample", C.c_void_p)]
 
 _P = C.c_void_p
 _H = C.c_void_p
@@ -62,6 +72,7 @@ _SIGS = {
     "corr_set_profiling": ([_H, C.c_int], C.c_int),
     "corr_read_profile": ([_H, _P, _P], C.c_int),
     "corr_launch_shape": ([_H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "corr_correlate_static": ([C.POINTER(CorrScanDesc), C.c_int64, _P, _P, _P], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -256,3 +267,34 @@ def from_scan(scan, streams=None, device_streams=None, nchan=None) -> Correlator
         for s, t in enumerate(device_streams):
             c.attach_device(s, t)
     return c
+
+
+class StaticScan:
+    """Descriptor for corr_correlate_static: a scan whose packed samples are
+    already in device memory (one CUDA tensor per station).  Holds the host
+    arrays the descriptor points to."""
+
+    MAXSEG = 64
+
+    def __init__(self, scan, dev_tensors, lut=(-3.336, -1.0, 1.0, 3.336)):
+        S = scan.stations
+        self._nu0 = np.ascontiguousarray(scan.nu0, dtype=np.float64)
+        self._nseg = np.array([len(p) for p in scan.polys], dtype=np.int32)
+        self._t0 = np.zeros((S, self.MAXSEG))
+        self._c = np.zeros((S, self.MAXSEG, 6))
+        for s, segs in enumerate(scan.polys):
+            for i, g in enumerate(segs):
+                self._t0[s, i] = g.t0
+                self._c[s, i, :] = g.coeffs
+        self._tensors = list(dev_tensors)
+        self._ptrs = (C.c_void_p * S)(*[t.data_ptr() for t in dev_tensors])
+        self._nb = np.array([t.numel() * t.element_size() for t in dev_tensors], dtype=np.uint64)
+        self._s0 = np.asarray(scan.sample0, dtype=np.int64).copy()
+        self.desc = CorrScanDesc(S, scan.nsub, scan.npol, scan.nchan, float(scan.fs), float(scan.tint),
+                                 (C.c_float * 4)(*lut), _ptr(self._nu0), _ptr(self._nseg), _ptr(self._t0),
+                                 _ptr(self._c), C.cast(self._ptrs, C.c_void_p), _ptr(self._nb), _ptr(self._s0))
+
+    def correlate(self, integration: int, dev_out, dev_weights=None, stream: Optional[int] = None) -> int:
+        return corr_correlate_static(C.byref(self.desc), int(integration), _ptr(dev_out), _ptr(dev_weights),
+                                     stream)
+
