@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--chunk-blocks", type=int, default=0, help="FFT blocks per F/X chunk (0: library default)")
+    ap.add_argument("--duration", type=float, default=10.0,
+                    help="scan length in seconds (10 s is the benchmark; shorter only for profiling)")
     return ap.parse_args()
 
 
@@ -144,9 +147,9 @@ def device_codes(nbytes: int, gen, device):
     return out
 
 
-def make_scan(seed):
+def make_scan(seed, duration=10.0):
     import synth
-    return synth.config2(seed=seed, duration=10.0, tint=1.0, boundary=5.0)
+    return synth.config2(seed=seed, duration=duration, tint=1.0, boundary=min(5.0, duration / 2))
 
 
 def samples_per_step(scan):
@@ -234,7 +237,7 @@ def main():
     _build.build()
     from paper_1502_06894_gb300 import corr
 
-    scan = make_scan(args.seed + rank)
+    scan = make_scan(args.seed + rank, args.duration)
     nint = int(round(scan.duration / scan.tint))
     gen = torch.Generator(device=dev)
     gen.manual_seed(1000 + args.seed + rank)
@@ -245,6 +248,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
 
     c = corr.from_scan(scan, device_streams=dstreams)
+    if args.chunk_blocks:
+        c.set_chunk_blocks(args.chunk_blocks)
     c.set_stream(stream.cuda_stream)
     c.flush()
     out = torch.empty((nint, scan.nbl, scan.G, scan.nchan), dtype=torch.complex64, device=dev)
@@ -339,6 +344,8 @@ def main():
         for h, t in zip(host, dstreams):
             h.copy_(t)
         c2 = corr.from_scan(scan)
+        if args.chunk_blocks:
+            c2.set_chunk_blocks(args.chunk_blocks)
         for s in range(S):
             c2.reserve(s, host[s].numel())
         out_h = torch.empty((nint, nbl, G, nch), dtype=torch.complex64, pin_memory=True)

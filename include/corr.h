@@ -89,6 +89,11 @@ int corr_set_sky_freq(corr_t *h, int subband, double nu0_hz);
 /* Arithmetic of the X step.  Only CORR_PREC_FP32 is accepted. */
 int corr_set_precision(corr_t *h, int mode);
 
+/* FFT blocks per F/X chunk (0, the default: as many as fit 1 GiB of FP32
+ * spectra, capped at one integration).  Smaller chunks keep the spectra in
+ * L2 between the F and X kernels.  Only before the first correlate call. */
+int corr_set_chunk_blocks(corr_t *h, int blocks);
+
 /* Run device work on this cudaStream_t (NULL: the handle's own stream). */
 int corr_set_stream(corr_t *h, void *cuda_stream);
 

@@ -53,6 +53,7 @@ _SIGS = {
     "corr_set_sky_freq": ([_H, C.c_int, C.c_double], C.c_int),
     "corr_set_precision": ([_H, C.c_int], C.c_int),
     "corr_set_stream": ([_H, _P], C.c_int),
+    "corr_set_chunk_blocks": ([_H, C.c_int], C.c_int),
     "corr_set_delay_poly": ([_H, C.c_int, C.c_double, _P], C.c_int),
     "corr_set_stream_start": ([_H, C.c_int, C.c_int64], C.c_int),
     "corr_reserve": ([_H, C.c_int, C.c_size_t], C.c_int),
@@ -143,6 +144,9 @@ class Correlator:
     # ---------------------------------------------------------------- setup
     def set_sky_freq(self, subband: int, nu0: float):
         self._check(corr_set_sky_freq(self.h, subband, float(nu0)))
+
+    def set_chunk_blocks(self, blocks: int):
+        self._check(corr_set_chunk_blocks(self.h, int(blocks)))
 
     def set_stream(self, stream_handle: int):
         self._check(corr_set_stream(self.h, stream_handle))

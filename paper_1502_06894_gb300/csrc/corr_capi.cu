@@ -81,6 +81,7 @@ struct corr_s {
   int* d_wcount = nullptr;
   double* d_wts = nullptr;
   size_t spec_budget = (size_t)1 << 30;
+  int chunk_req = 0;  // blocks per F/X chunk requested by the caller (0: from spec_budget)
 
   // optional per-stage CUDA-event timing of the launches
   bool profiling = false;
@@ -240,7 +241,7 @@ static int prepare(corr_t* h) {
   const int S = h->S, G = h->G, nch = h->nchan, nbl = nbl_of(S);
   h->Mcap = (int)((h->spi + h->N - 1) / h->N) + 1;
   const size_t per_block = (size_t)G * S * nch * sizeof(float2);
-  int64_t cb = (int64_t)(h->spec_budget / per_block);
+  int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
   if (cb < 1) cb = 1;
   if (cb > h->Mcap) cb = h->Mcap;
   h->CB = (int)cb;
@@ -531,6 +532,14 @@ int corr_set_precision(corr_t* h, int mode) {
   if (!h) return CORR_EINVAL;
   if (mode != CORR_PREC_FP32) return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
   h->precision = mode;
+  return CORR_OK;
+}
+
+int corr_set_chunk_blocks(corr_t* h, int blocks) {
+  if (!h) return CORR_EINVAL;
+  if (h->prepared) return h->fail(CORR_ESTATE, "corr_set_chunk_blocks: only before the first correlate");
+  if (blocks < 0) return h->fail(CORR_EINVAL, "corr_set_chunk_blocks: blocks must be >= 0");
+  h->chunk_req = blocks;
   return CORR_OK;
 }
 

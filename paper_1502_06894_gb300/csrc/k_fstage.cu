@@ -153,13 +153,51 @@ template <int L> struct Groups {
 
 constexpr int kBufPad(int L) { return L + L / 32 + 1; }
 
+// Byte offset of the packed-word staging area after the NGRP FFT buffers,
+// rounded up to 16 bytes for the 16-byte shared-memory stores.
+constexpr size_t kWordsOffset(int L, int NGRP) {
+  return ((size_t)NGRP * kBufPad(L) * sizeof(float2) + 15) & ~(size_t)15;
+}
+
 __host__ __device__ inline int wslot_words(int N, int G) {
   // window bits 2*N*G plus up to 31 bits of misalignment, plus one spare word
   return (((2 * N * G + 31 + 31) >> 5) + 1 + 3) & ~3;
 }
 
-template <int L>
-__global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP)
+// Compile-time stream count GC (0: runtime p.G).  With GC = 16 a sample-time
+// group is exactly one 32-bit word (a sample pair is one 64-bit load when
+// the window starts on an even word); with GC = 32 it is two words.
+template <int GC>
+__device__ __forceinline__ void load_pair(const uint32_t* __restrict__ wsl, int boff, int G, int m, int j,
+                                          bool even, uint32_t& c0, uint32_t& c1) {
+  if constexpr (GC == 16) {
+    uint32_t w0, w1;
+    if (even) {
+      const uint2 w = *reinterpret_cast<const uint2*>(wsl + 2 * m);
+      w0 = w.x;
+      w1 = w.y;
+    } else {
+      w0 = wsl[2 * m];
+      w1 = wsl[2 * m + 1];
+    }
+    c0 = (w0 >> (2 * j)) & 3u;
+    c1 = (w1 >> (2 * j)) & 3u;
+  } else if constexpr (GC == 32) {
+    const int q = 4 * m + (j >> 4);
+    c0 = (wsl[q] >> (2 * (j & 15))) & 3u;
+    c1 = (wsl[q + 2] >> (2 * (j & 15))) & 3u;
+  } else {
+    const int bit = boff + 2 * (2 * m * G + j);
+    c0 = (wsl[bit >> 5] >> (bit & 31)) & 3u;
+    const int bit1 = bit + 2 * G;
+    c1 = (wsl[bit1 >> 5] >> (bit1 & 31)) & 3u;
+  }
+}
+
+template <int L> struct MinBlocks { static constexpr int v = (L >= 512 && L <= 1024) ? 2 : 1; };
+
+template <int L, int GC>
+__global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)
 k_fstage(FParams p, int slots, int wslot) {
   using P = Plan<L>;
   constexpr int T = P::T;
@@ -172,14 +210,15 @@ k_fstage(FParams p, int slots, int wslot) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(fbuf_all + NGRP * BUF);
+  static_assert(kWordsOffset(L, NGRP) % 16 == 0, "staging area must be 16-byte aligned");
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + kWordsOffset(L, NGRP));
 
   const int tid = threadIdx.x;
   const int grp = tid / T;
   const int t = tid - grp * T;
   float2* fbuf = fbuf_all + grp * BUF;
   const int s = blockIdx.y;
-  const int G = p.G;
+  const int G = GC ? GC : p.G;
   const StationView sv = p.st[s];
 
   const int bb0 = blockIdx.x * slots;
@@ -189,7 +228,8 @@ k_fstage(FParams p, int slots, int wslot) {
   __shared__ int s_boff[64];
   __shared__ int s_ok[64];
 
-  // ---- stage the windows of this CTA's blocks ----
+  // ---- stage the windows of this CTA's blocks (16-byte loads where the
+  //      words lie inside the station's data, single words at its end) ----
   for (int sl = 0; sl < nslots; ++sl) {
     const int d = p.blk0 + bb0 + sl;
     const bool ok = p.valid[(size_t)s * p.ld + d] != 0;
@@ -201,14 +241,28 @@ k_fstage(FParams p, int slots, int wslot) {
       w0 = bit0 >> 5;
       boff = (int)(bit0 & 31);
       nw = (boff + 2 * N * G + 31) >> 5;
-      if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);  // last word may be absent when it holds no window bit
+      if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);
     }
-    if (tid == 0) {
-      s_boff[sl] = boff;
-      s_ok[sl] = ok ? 1 : 0;
-    }
+    // read from the 16-byte aligned word a0 = w0 & ~3 onwards (dst[q] = word
+    // a0 + q), single words at the end of the data
+    if (tid == 0) s_ok[sl] = ok ? 1 : 0;
     uint32_t* dst = wbuf + sl * wslot;
-    for (int q = tid; q < nw; q += blockDim.x) dst[q] = __ldg(&sv.words[w0 + q]);
+    const int lead = (int)(w0 & 3);
+    const int64_t a0 = w0 - lead;
+    const int ntot = nw + lead;
+    const int nvec = ntot >> 2;
+    const uint4* src4 = reinterpret_cast<const uint4*>(sv.words + a0);
+    for (int q = tid; q < nvec; q += blockDim.x) {
+      if (a0 + 4 * q + 4 <= sv.nwords) {
+        reinterpret_cast<uint4*>(dst)[q] = __ldg(src4 + q);
+      } else {
+        for (int u = 0; u < 4; ++u)
+          if (a0 + 4 * q + u < sv.nwords) dst[4 * q + u] = __ldg(&sv.words[a0 + 4 * q + u]);
+      }
+    }
+    for (int q = 4 * nvec + tid; q < ntot; q += blockDim.x)
+      if (a0 + q < sv.nwords) dst[q] = __ldg(&sv.words[a0 + q]);
+    if (tid == 0) s_boff[sl] = boff + 32 * lead;  // bit offset from word a0
   }
   __syncthreads();
 
@@ -220,8 +274,11 @@ k_fstage(FParams p, int slots, int wslot) {
     const int sl = active ? task / G : 0;
     const int j = active ? task - sl * G : 0;
     const bool ok = active && s_ok[sl];
-    const uint32_t* wsl = wbuf + sl * wslot;
     const int boff = s_boff[sl];
+    // for GC = 16 / 32 the window starts on a word boundary: skip the lead
+    // words; a sample pair is then one 64-bit load when that start is even
+    const uint32_t* wsl = wbuf + sl * wslot + (GC ? (boff >> 5) : 0);
+    const bool even = ((boff >> 5) & 1) == 0;
 
     // ---- pass 0: unpack straight into registers (NS = 1, no twiddles) ----
     {
@@ -234,10 +291,8 @@ k_fstage(FParams p, int slots, int wslot) {
           const int m = jj + r * (L / R0);
           float x0 = 0.f, x1 = 0.f;
           if (ok) {
-            const int bit = boff + 2 * (2 * m * G + j);
-            const uint32_t c0 = (wsl[bit >> 5] >> (bit & 31)) & 3u;
-            const int bit1 = bit + 2 * G;
-            const uint32_t c1 = (wsl[bit1 >> 5] >> (bit1 & 31)) & 3u;
+            uint32_t c0, c1;
+            load_pair<GC>(wsl, boff, G, m, j, even, c0, c1);
             x0 = level(c0, l0, l1, l2, l3);
             x1 = level(c1, l0, l1, l2, l3);
           }
@@ -257,39 +312,53 @@ k_fstage(FParams p, int slots, int wslot) {
     if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
 
     // ---- real split, rotation, store ----
+    // channels k and L-k come from the same pair Z[k], Z[L-k]:
+    //   X[k] = E + W O,  X[L-k] = conj(E - W O),  W = W_N^k
     if (active) {
       const int d = p.blk0 + bb0 + sl;
       const int bb = bb0 + sl;
       const float delta = p.delta[(size_t)s * p.ld + d];
       const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
       float2* out = reinterpret_cast<float2*>(p.out) + (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
+      constexpr int HALF = L / 2;
+      constexpr int QN = HALF / T + 1;  // k runs over 0..HALF
 #pragma unroll 4
-      for (int q = 0; q < L / T; ++q) {
+      for (int q = 0; q < QN; ++q) {
         const int k = t + q * T;
-        float2 X = make_float2(0.f, 0.f);
+        if (k > HALF) break;
+        float2 Xa = make_float2(0.f, 0.f), Xb = make_float2(0.f, 0.f);
+        const int km = (L - k) & (L - 1);
         if (ok) {
           const float2 Zk = fbuf[pad32(k)];
-          const float2 Zm = fbuf[pad32((L - k) & (L - 1))];
-          // E = (Zk + conj Zm)/2 ; O = (Zk - conj Zm)/(2i)
+          const float2 Zm = fbuf[pad32(km)];
           const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
           const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
           const float2 w = __ldg(&p.twN[k]);
-          X = make_float2(E.x + (w.x * O.x - w.y * O.y), E.y + (w.x * O.y + w.y * O.x));
+          const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
+          Xa = make_float2(E.x + WO.x, E.y + WO.y);
+          Xb = make_float2(E.x - WO.x, WO.y - E.y);
+          // rotation exp(+2 pi i (phi + k delta)); the argument is reduced to
+          // [-pi, pi] first, where the fast sine/cosine is accurate to ~4e-7
           float ph = fmaf((float)k, delta, phi);
           ph -= rintf(ph);
           float sn, cs;
-          sincospif(2.0f * ph, &sn, &cs);
-          X = make_float2(X.x * cs - X.y * sn, X.x * sn + X.y * cs);
+          __sincosf(6.28318530717958648f * ph, &sn, &cs);
+          Xa = make_float2(Xa.x * cs - Xa.y * sn, Xa.x * sn + Xa.y * cs);
+          float ph2 = fmaf((float)km, delta, phi);
+          ph2 -= rintf(ph2);
+          __sincosf(6.28318530717958648f * ph2, &sn, &cs);
+          Xb = make_float2(Xb.x * cs - Xb.y * sn, Xb.x * sn + Xb.y * cs);
         }
-        out[k] = X;
+        out[k] = Xa;
+        if (k != 0 && k != HALF) out[km] = Xb;
       }
     }
     gsync<T>(grp);
   }
 }
 
-template <int L>
-static cudaError_t launch_L(const FParams& p, cudaStream_t st) {
+template <int L, int GC>
+static cudaError_t launch_LG(const FParams& p, cudaStream_t st) {
   constexpr int T = Plan<L>::T;
   constexpr int NGRP = Groups<L>::NGRP;
   const int N = 2 * L;
@@ -297,13 +366,22 @@ static cudaError_t launch_L(const FParams& p, cudaStream_t st) {
   if (slots < 1) slots = 1;
   if (slots > 64) slots = 64;
   const int wslot = wslot_words(N, p.G);
-  const size_t smem = (size_t)NGRP * kBufPad(L) * sizeof(float2) + (size_t)slots * wslot * sizeof(uint32_t);
+  const size_t smem = kWordsOffset(L, NGRP) + (size_t)slots * wslot * sizeof(uint32_t);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_fstage<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_fstage<L, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((p.CB + slots - 1) / slots, p.S);
-  k_fstage<L><<<grid, T * NGRP, smem, st>>>(p, slots, wslot);
+  k_fstage<L, GC><<<grid, T * NGRP, smem, st>>>(p, slots, wslot);
   return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_L(const FParams& p, cudaStream_t st) {
+  if constexpr (L >= 256) {
+    if (p.G == 16) return launch_LG<L, 16>(p, st);
+    if (p.G == 32) return launch_LG<L, 32>(p, st);
+  }
+  return launch_LG<L, 0>(p, st);
 }
 
 bool fstage_supported(int nchan) {
