@@ -26,6 +26,7 @@ CORR_ESTATE = -6
 CORR_EEND = -7
 CORR_ETOOBIG = -8
 CORR_PREC_FP32 = 0
+CORR_PREC_FP16_TC = 1
 
 _ERRNAMES = {0: "CORR_OK", -1: "CORR_EINVAL", -2: "CORR_ENOMEM", -3: "CORR_EAGAIN", -4: "CORR_ETIMEOUT",
              -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND", -8: "CORR_ETOOBIG"}
@@ -144,6 +145,9 @@ class Correlator:
     # ---------------------------------------------------------------- setup
     def set_sky_freq(self, subband: int, nu0: float):
         self._check(corr_set_sky_freq(self.h, subband, float(nu0)))
+
+    def set_precision(self, mode: int):
+        self._check(corr_set_precision(self.h, int(mode)))
 
     def set_chunk_blocks(self, blocks: int):
         self._check(corr_set_chunk_blocks(self.h, int(blocks)))

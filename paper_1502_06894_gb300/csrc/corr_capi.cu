@@ -82,6 +82,11 @@ struct corr_s {
   double* d_wts = nullptr;
   size_t spec_budget = (size_t)1 << 30;
   int chunk_req = 0;  // blocks per F/X chunk requested by the caller (0: from spec_budget)
+  int sm_count = 0;
+  int KZ_tc = 0;      // tensor-core partial sums per chunk (<= 256 blocks each)
+  int sigma = 0;      // FP16 spectra carry X * 2^-sigma
+  int* d_err = nullptr;
+  int* h_err = nullptr;  // pinned
 
   // optional per-stage CUDA-event timing of the launches
   bool profiling = false;
@@ -206,6 +211,10 @@ static void free_device(corr_t* h) {
   cudaFree(h->d_wcount);
   cudaFree(h->d_wts);
   h->d_wts = nullptr;
+  cudaFree(h->d_err);
+  cudaFreeHost(h->h_err);
+  h->d_err = nullptr;
+  h->h_err = nullptr;
   h->d_views = nullptr; h->h_views = nullptr; h->d_nseg = nullptr; h->d_seg_t0 = nullptr;
   h->d_seg_c = nullptr; h->d_nu0 = nullptr; h->d_start = nullptr; h->d_delta = nullptr;
   h->d_phi = nullptr; h->d_valid = nullptr; h->d_stat = nullptr; h->h_stat = nullptr;
@@ -246,6 +255,14 @@ static int prepare(corr_t* h) {
   if (cb > h->Mcap) cb = h->Mcap;
   h->CB = (int)cb;
   h->KZ = xstage_kz(h->CB, S, G, nch);
+  h->KZ_tc = (h->CB + 255) / 256;
+  {
+    int lg = 0;
+    while ((1 << (lg + 1)) <= h->N) ++lg;
+    h->sigma = lg / 2;
+  }
+  CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev), "SM count");
+  const int kz_alloc = h->KZ > h->KZ_tc ? h->KZ : h->KZ_tc;
   int rc;
   if ((rc = dalloc(h, (void**)&h->d_views, sizeof(StationView) * S, "views"))) return rc;
   CK(cudaMallocHost((void**)&h->h_views, sizeof(StationView) * S), "cudaMallocHost views");
@@ -261,10 +278,14 @@ static int prepare(corr_t* h) {
   CK(cudaMallocHost((void**)&h->h_stat, sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
   if ((rc = dalloc(h, (void**)&h->d_twN, sizeof(float2) * h->N, "twiddles"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_spec, per_block * h->CB, "spectra"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_part, sizeof(float2) * (size_t)h->KZ * nbl * G * nch, "partials"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_part, sizeof(float2) * (size_t)kz_alloc * nbl * G * nch, "partials"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_out, sizeof(float2) * (size_t)nbl * G * nch, "out"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wcount, sizeof(int) * nbl, "wcount"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wts, sizeof(double) * nbl, "weights"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_err, sizeof(int), "error flag"))) return rc;
+  CK(cudaMallocHost((void**)&h->h_err, sizeof(int)), "cudaMallocHost err");
+  *h->h_err = 0;
+  CK(cudaMemset(h->d_err, 0, sizeof(int)), "error flag reset");
   // W_N^m = exp(-2 pi i m / N), computed in FP64 on the host
   std::vector<float2> tw(h->N);
   for (int m = 0; m < h->N; ++m) {
@@ -358,6 +379,7 @@ static FParams fparams(corr_t* h, int blk0, int cb) {
   p.lut3 = h->lut[3];
   p.twN = h->d_twN;
   p.out_kind = 0;
+  p.scale = 1.0f;
   p.out = h->d_spec;
   return p;
 }
@@ -390,6 +412,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   CK(cudaMemcpyAsync(h->h_stat, h->d_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyDeviceToHost, h->stream),
      "stat D2H");
   CK(cudaStreamSynchronize(h->stream), "delay_blocks");
+  if (*h->h_err) return h->fail(CORR_ETIMEOUT, "a tensor-core X-step wait timed out on the device");
   const unsigned long long off = 1ull << 62;
   bool any_data = false;
   for (int s = 0; s < S; ++s) {
@@ -405,30 +428,54 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
 
   // 2. F and X per chunk
   const int nbl = nbl_of(S);
-  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)h->KZ * nbl * h->G * h->nchan, h->stream),
+  const int kz_used = h->precision == CORR_PREC_FP16_TC ? h->KZ_tc : h->KZ;
+  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, h->stream),
      "partials memset");
+  const bool tc = h->precision == CORR_PREC_FP16_TC;
   for (int c0 = 0; c0 < M; c0 += h->CB) {
     const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
     FParams fp = fparams(h, c0, cb);
+    if (tc) {
+      fp.out_kind = 1;
+      fp.scale = ldexpf(1.0f, -h->sigma);
+    }
     pa = prof_begin(h);
     CK(launch_fstage(fp, h->stream), "fstage launch");
     prof_end(h, 1, pa);
-    XParams xp;
-    xp.spec = h->d_spec;
-    xp.CB = cb;
-    xp.S = S;
-    xp.G = h->G;
-    xp.nchan = h->nchan;
-    xp.KZ = h->KZ;
-    xp.part = h->d_part;
-    pa = prof_begin(h);
-    CK(launch_xstage(xp, h->stream), "xstage launch");
-    prof_end(h, 2, pa);
+    if (tc) {
+      XTCParams xp;
+      xp.spec = reinterpret_cast<const __half2*>(h->d_spec);
+      xp.CB = cb;
+      xp.cb = cb;
+      xp.kblocks = 256;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.cpt = xtc_cpt(S);
+      xp.W = 2 * xp.cpt;
+      xp.part = h->d_part;
+      xp.err = h->d_err;
+      pa = prof_begin(h);
+      CK(launch_xtc(xp, h->sm_count, h->stream), "tensor-core xstage launch");
+      prof_end(h, 2, pa);
+    } else {
+      XParams xp;
+      xp.spec = h->d_spec;
+      xp.CB = cb;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.KZ = h->KZ;
+      xp.part = h->d_part;
+      pa = prof_begin(h);
+      CK(launch_xstage(xp, h->stream), "xstage launch");
+      prof_end(h, 2, pa);
+    }
   }
   // 3. weights + normalisation
   FinParams fin;
   fin.part = h->d_part;
-  fin.KZ = h->KZ;
+  fin.KZ = kz_used;
   fin.S = S;
   fin.G = h->G;
   fin.nchan = h->nchan;
@@ -441,8 +488,12 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   fin.weights = w_out;
   pa = prof_begin(h);
   CK(launch_weights(fin, h->stream), "weights launch");
-  CK(launch_finalize(fin, h->stream), "finalize launch");
+  if (tc)
+    CK(launch_finalize_tc(fin, ldexpf(1.0f, 2 * h->sigma), h->stream), "finalize launch");
+  else
+    CK(launch_finalize(fin, h->stream), "finalize launch");
   prof_end(h, 3, pa);
+  if (tc) CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "error flag D2H");
   h->next_int = i + 1;
   return CORR_OK;
 }
@@ -530,7 +581,12 @@ int corr_set_sky_freq(corr_t* h, int subband, double nu0_hz) {
 
 int corr_set_precision(corr_t* h, int mode) {
   if (!h) return CORR_EINVAL;
-  if (mode != CORR_PREC_FP32) return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
+  if (mode != CORR_PREC_FP32 && mode != CORR_PREC_FP16_TC)
+    return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
+  if (mode == CORR_PREC_FP16_TC && h->S > 64)
+    return h->fail(CORR_EINVAL, "corr_set_precision: the tensor-core X step takes at most 64 stations");
+  if (h->prepared && mode != h->precision)
+    return h->fail(CORR_ESTATE, "corr_set_precision: only before the first correlate");
   h->precision = mode;
   return CORR_OK;
 }
@@ -672,6 +728,7 @@ int corr_correlate(corr_t* h, float* out, double* weights) {
       e = cudaMemcpyAsync(weights, dw, sizeof(double) * nbl_of(h->S), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rc = h->cuda_fail(e, "correlate D2H");
+    else if (*h->h_err) rc = h->fail(CORR_ETIMEOUT, "a tensor-core X-step wait timed out on the device");
   }
   return rc;
 }

@@ -3,6 +3,7 @@
 // (unpack + FFT + rotation), the X stage (cross-multiply-accumulate) and the
 // finalisation (weights, normalisation).
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,8 +58,22 @@ struct FParams {
   int S, G, npol, nsub, nchan;
   float lut0, lut1, lut2, lut3;
   const float2* twN;        // W_N^m, m < N
-  int out_kind;             // 0: complex FP32 spectra
+  int out_kind;             // 0: complex FP32 spectra; 1: complex FP16 spectra times `scale`
+  float scale;              // exact power of two (FP16 output only)
   void* out;                // [G][CB][S][nchan]
+};
+
+// X step on tensor cores: FP16 spectra in, FP32 partial sums out.
+struct XTCParams {
+  const __half2* spec;      // [G][CB][S][nchan]
+  int CB;                   // blocks per stream in the spectra buffer
+  int cb;                   // blocks present in this chunk
+  int kblocks;              // blocks per partial sum (a multiple of 64, <= 256)
+  int S, G, nchan;
+  int cpt;                  // channels per 128-row tile (floor(64/S))
+  int W;                    // channels per work item (2 * cpt)
+  float2* part;             // [KZ][G][nchan][nbl], KZ = ceil(cb / kblocks)
+  int* err;                 // set to 1 when a device wait times out
 };
 
 // X stage: V_ab[k] += X_a[k] conj(X_b[k]) over the chunk's blocks.
@@ -90,6 +105,11 @@ int xstage_kz(int CB, int S, int G, int nchan);
 cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
 cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, cudaStream_t s);
+int xtc_cpt(int S);
+size_t xtc_smem_bytes(int S);
+cudaError_t launch_xtc(const XTCParams& p, int sm_count, cudaStream_t s);
+// finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale
+cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s);
 
 __host__ __device__ inline int nbl_of(int S) { return S * (S + 1) / 2; }
 __host__ __device__ inline int bl_index(int a, int b, int S) { return a * S - a * (a - 1) / 2 + (b - a); }

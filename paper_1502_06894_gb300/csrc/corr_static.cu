@@ -198,6 +198,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     fp.lut3 = d->lut[3];
     fp.twN = (const float2*)(base + o_tw);
     fp.out_kind = 0;
+    fp.scale = 1.0f;
     fp.out = base + o_spec;
     e = launch_fstage(fp, st);
     if (e != cudaSuccess) break;

@@ -64,4 +64,35 @@ cudaError_t launch_finalize(const FinParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Tensor-core partial sums are laid out [KZ][G][nchan][nbl] (baseline
+// fastest, as the X kernel's epilogue writes them).
+__global__ void k_finalize_tc(FinParams p, float unscale) {
+  const int nbl = nbl_of(p.S);
+  const size_t per = (size_t)p.G * p.nchan;
+  const size_t total = (size_t)nbl * per;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int bl = (int)(e / per);
+    const size_t gk = e - (size_t)bl * per;  // g * nchan + k
+    float2 v = make_float2(0.f, 0.f);
+    for (int kz = 0; kz < p.KZ; ++kz) {
+      const float2 x = p.part[((size_t)kz * per + gk) * nbl + bl];
+      v.x += x.x;
+      v.y += x.y;
+    }
+    const int w = p.wcount[bl];
+    const float sc = w > 0 ? (float)((double)unscale / ((double)w * (double)p.N)) : 0.f;
+    p.out[e] = make_float2(v.x * sc, v.y * sc);
+  }
+}
+
+cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s) {
+  const size_t total = (size_t)nbl_of(p.S) * p.G * p.nchan;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_finalize_tc<<<blocks, 256, 0, s>>>(p, unscale);
+  return cudaGetLastError();
+}
+
 }  // namespace corr

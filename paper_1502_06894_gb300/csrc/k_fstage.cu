@@ -16,7 +16,8 @@
 //            O = (Z[k] - conj Z[L-k])/(2i), k = 0..N/2-1 (Nyquist dropped);
 //   rotate   X[k] *= exp(+2 pi i (phi + k*delta)), phi = frac(nu0 tau) and
 //            delta = eps*fs/N from the FP64 delay kernel, FP32 within the block;
-//   store    complex FP32 spectra [stream][block][station][channel].
+//   store    complex FP32 spectra [stream][block][station][channel], or for the
+//            tensor-core X step complex FP16 times an exact power of two.
 //
 // Blocks that are not valid at this station (window outside the data, or no
 // delay segment yet) store zeros, so they add nothing in the X step.
@@ -349,8 +350,14 @@ k_fstage(FParams p, int slots, int wslot) {
           __sincosf(6.28318530717958648f * ph2, &sn, &cs);
           Xb = make_float2(Xb.x * cs - Xb.y * sn, Xb.x * sn + Xb.y * cs);
         }
-        out[k] = Xa;
-        if (k != 0 && k != HALF) out[km] = Xb;
+        if (p.out_kind == 1) {
+          __half2* o16 = reinterpret_cast<__half2*>(p.out) + (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
+          o16[k] = __floats2half2_rn(Xa.x * p.scale, Xa.y * p.scale);
+          if (k != 0 && k != HALF) o16[km] = __floats2half2_rn(Xb.x * p.scale, Xb.y * p.scale);
+        } else {
+          out[k] = Xa;
+          if (k != 0 && k != HALF) out[km] = Xb;
+        }
       }
     }
     gsync<T>(grp);

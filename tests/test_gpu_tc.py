@@ -1,0 +1,113 @@
+"""The FP16 tensor-core X step (tcgen05, FP32 accumulation in TMEM) against
+the FP64 oracle.
+
+Stated bound: relative RMS per baseline <= 1.5e-3 (FP16 keeps 11 significant
+bits; each spectrum value carries a relative rounding error up to 2^-11 and
+the cross-products inherit about twice that, averaged down over blocks and
+channels).  Weights are exact: validity is integer work shared with the FP32
+path.  The measured errors are printed for the record.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP16 = 1.5e-3
+
+
+@pytest.fixture(scope="module")
+def corr():
+    from paper_1502_06894_gb300 import _build
+    _build.build()
+    from paper_1502_06894_gb300 import corr as c
+    return c
+
+
+def rel_rms_per_baseline(v, ref):
+    v = v.reshape(v.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=1) / np.sum(np.abs(ref) ** 2, axis=1))
+
+
+def run_tc(corr, sc, streams, nint):
+    c = corr.from_scan(sc, streams)
+    c.set_precision(corr.CORR_PREC_FP16_TC)
+    outs, ws = [], []
+    for _ in range(nint):
+        r = c.correlate()
+        assert r is not None
+        outs.append(r[0])
+        ws.append(r[1])
+    c.close()
+    return np.stack(outs), np.stack(ws)
+
+
+def check(sc, vis, w, ref, wref, nint, label):
+    assert np.array_equal(w, wref)
+    worst = 0.0
+    for i in range(nint):
+        err = rel_rms_per_baseline(vis[i].reshape(sc.nbl, sc.G, sc.nchan), ref[i])
+        worst = max(worst, float(err.max()))
+        assert np.all(err < TOL_FP16), (label, i, err.max())
+    print("%s: FP16 tensor-core X step, max rel-RMS per baseline %.3e" % (label, worst))
+    return worst
+
+
+def test_tc_config2_slice(corr):
+    """10 stations, 8 subbands x 2 pols, 1024 channels: 6 channels of 20
+    rows per 128-row tile, 12-channel work items, a 0.05 s integration of
+    781.25 blocks (ragged last K tile)."""
+    sc = synth.config2(seed=2, duration=0.1, tint=0.05, boundary=0.05)
+    streams = [synth.station_bytes(sc, s, physics=False) for s in range(sc.stations)]
+    ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
+    vis, w = run_tc(corr, sc, streams, 2)
+    check(sc, vis, w, ref, wref, 2, "cfg2 slice")
+
+
+def test_tc_64_stations(corr):
+    """64 stations fill a whole 128-row tile with one channel (config-3
+    station count, 4096 channels, 64 Msample/s), two integrations of 130.5
+    blocks."""
+    fs = 64e6
+    N = 8192
+    tint = 130.5 * N / fs
+    sc = synth.config2(seed=3, duration=2 * tint, tint=tint, boundary=tint, nchan=4096, stations=64, nsub=1, npol=1,
+                       fs=fs, nu0_base=1.6e9)
+    streams = [synth.station_bytes(sc, s, physics=False) for s in range(sc.stations)]
+    ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
+    vis, w = run_tc(corr, sc, streams, 2)
+    check(sc, vis, w, ref, wref, 2, "64 stations")
+
+
+@pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (128, 33, 1, 1)])
+def test_tc_shapes(corr, nchan, S, nsub, npol):
+    """Tiles of 32, 21, 9 and 1 channels, odd stream counts, a slice wider
+    than the band, 8-byte copies."""
+    fs = 32e6
+    N = 2 * nchan
+    tint = round((300 * N + 5) / fs * fs) / fs
+    sc = synth.config2(seed=nchan + S, duration=2 * tint, tint=tint, boundary=tint, nchan=nchan, stations=S,
+                       nsub=nsub, npol=npol)
+    streams = [synth.station_bytes(sc, s, physics=False) for s in range(S)]
+    ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
+    vis, w = run_tc(corr, sc, streams, 2)
+    check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d" % (S, nchan, nsub * npol))
+
+
+def test_tc_two_bit_efficiency_config1(corr, cfg1):
+    """End to end through the tensor-core path: the band-averaged normalised
+    cross-correlation of config 1 equals eta * rho (Bussgang, 2-bit at
+    +-0.98 sigma), as on the FP64 oracle."""
+    import math
+    sc, streams, o = cfg1
+    vis, w = run_tc(corr, sc, streams, 1)
+    v = vis[0].reshape(sc.nbl, sc.G, sc.nchan)[:, 0, :]
+    k = slice(8, 224)
+    r = np.mean(v[1, k] / np.sqrt(v[0, k].real * v[2, k].real))
+    p_in = math.erf(0.98 / math.sqrt(2))
+    eta = (2 / math.pi) * (1 + 2.336 * math.exp(-0.98 ** 2 / 2)) ** 2 / (p_in + 3.336 ** 2 * (1 - p_in))
+    sigma = 1.0 / math.sqrt(62500 * (k.stop - k.start))
+    assert abs(r.real - eta * sc.rho) < 4 * sigma, (r, eta * sc.rho)
