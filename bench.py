@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tc", action="store_true", help="skip the FP16 tensor-core leg")
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--chunk-blocks", type=int, default=0, help="FFT blocks per F/X chunk (0: library default)")
     ap.add_argument("--duration", type=float, default=10.0,
@@ -247,27 +248,8 @@ def main():
     # a dedicated stream: the library's launches and the timing events share it
     stream = torch.cuda.Stream(device=dev)
 
-    c = corr.from_scan(scan, device_streams=dstreams)
-    if args.chunk_blocks:
-        c.set_chunk_blocks(args.chunk_blocks)
-    c.set_stream(stream.cuda_stream)
-    c.flush()
     out = torch.empty((nint, scan.nbl, scan.G, scan.nchan), dtype=torch.complex64, device=dev)
     wts = torch.empty((nint, scan.nbl), dtype=torch.float64, device=dev)
-
-    def step():
-        c.rewind()
-        for i in range(nint):
-            rc = c.correlate_device(out[i], wts[i])
-            if rc != corr.CORR_OK:
-                raise RuntimeError("correlate_device returned %d" % rc)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    c.read_profile()
-    c.set_profiling(True)
-    clk = Clocks(dev.index)
 
     def barrier():
         if ws > 1:
@@ -275,27 +257,55 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    barrier()
-    clk.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    prof = c.read_profile()
-    c.set_profiling(False)
-    cb, kz = c.launch_shape()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def device_leg(precision):
+        """Time K steps of the device-resident path at one precision."""
+        c = corr.from_scan(scan, device_streams=dstreams)
+        if args.chunk_blocks:
+            c.set_chunk_blocks(args.chunk_blocks)
+        c.set_precision(precision)
+        c.set_stream(stream.cuda_stream)
+        c.flush()
+
+        def step():
+            c.rewind()
+            for i in range(nint):
+                rc = c.correlate_device(out[i], wts[i])
+                if rc != corr.CORR_OK:
+                    raise RuntimeError("correlate_device returned %d" % rc)
+
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        c.read_profile()
+        c.set_profiling(True)
+        clk = Clocks(dev.index)
+        barrier()
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1) / args.steps
+        prof = c.read_profile()
+        shape = c.launch_shape()
+        c.close()
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, prof, clocks, shape
+
+    ms, prof, clocks, (cb, kz) = device_leg(corr.CORR_PREC_FP32)
     sps = samples_per_step(scan)
     value = sps * ws / (ms / 1e3)
+    tc = None
+    if not args.no_tc:
+        ms_tc, prof_tc, clocks_tc, _ = device_leg(corr.CORR_PREC_FP16_TC)
 
     # ---- roofline of the dominant kernel ----
     peak_hbm, peak_src = measured_peaks()
@@ -336,6 +346,19 @@ def main():
                  "launch_ms": t_launch * 1e3, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
     launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
+    if not args.no_tc:
+        xt_ms, xt_n = prof_tc["xstage"]
+        ft_ms, ft_n = prof_tc["fstage"]
+        # FP16 spectra: 2 B read per station-sample in the X step
+        xt_bytes = steps * ss_step * 2.0
+        tc = {"value": sps * ws / (ms_tc / 1e3), "unit": METRIC, "ms_per_step": ms_tc, "dtype": "f16 in, f32 accumulate",
+              "error_bound_rel_rms": 1.5e-3, "measured_rel_rms": "3.0e-4 .. 3.5e-4 (GPU parity tests)",
+              "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
+              "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
+              "xstep_hbm_gbs": xt_bytes / (xt_ms / 1e3) / 1e9 if xt_ms > 0 else None,
+              "xstep_vs_fp32_xstep": (x_ms / xt_ms) if xt_ms > 0 else None,
+              "stages": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k, v in prof_tc.items()},
+              "clocks": clocks_tc}
 
     # ---- end to end through the host API ----
     e2e = None
@@ -389,7 +412,6 @@ def main():
                "sample": "first %.1f s of the scan as one integration, all stations and streams (%.1f s wall)"
                          % (CPU_SAMPLE_S, dt)}
 
-    c.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -401,7 +423,7 @@ def main():
                            "chunk_blocks": cb, "x_partials": kz,
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops}
+                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

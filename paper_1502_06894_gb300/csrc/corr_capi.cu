@@ -17,6 +17,8 @@
 using namespace corr;
 
 constexpr int kStages = 4;  // delay blocks, F, X, weights+finalise
+// blocks accumulated in tensor memory (FP32) before the partial sum in HBM
+constexpr int kTcBlocks = 1024;
 
 namespace {
 
@@ -87,6 +89,8 @@ struct corr_s {
   int sigma = 0;      // FP16 spectra carry X * 2^-sigma
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned
+  unsigned char* d_tiles = nullptr;  // tensor-core operand tiles (FFT length <= 2048)
+  bool tc_tiles = false;
 
   // optional per-stage CUDA-event timing of the launches
   bool profiling = false;
@@ -213,6 +217,8 @@ static void free_device(corr_t* h) {
   h->d_wts = nullptr;
   cudaFree(h->d_err);
   cudaFreeHost(h->h_err);
+  cudaFree(h->d_tiles);
+  h->d_tiles = nullptr;
   h->d_err = nullptr;
   h->h_err = nullptr;
   h->d_views = nullptr; h->h_views = nullptr; h->d_nseg = nullptr; h->d_seg_t0 = nullptr;
@@ -255,7 +261,7 @@ static int prepare(corr_t* h) {
   if (cb > h->Mcap) cb = h->Mcap;
   h->CB = (int)cb;
   h->KZ = xstage_kz(h->CB, S, G, nch);
-  h->KZ_tc = (h->CB + 255) / 256;
+  h->KZ_tc = (h->CB + kTcBlocks - 1) / kTcBlocks;
   {
     int lg = 0;
     while ((1 << (lg + 1)) <= h->N) ++lg;
@@ -284,6 +290,16 @@ static int prepare(corr_t* h) {
   if ((rc = dalloc(h, (void**)&h->d_wts, sizeof(double) * nbl, "weights"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_err, sizeof(int), "error flag"))) return rc;
   CK(cudaMallocHost((void**)&h->h_err, sizeof(int)), "cudaMallocHost err");
+  h->tc_tiles = h->precision == CORR_PREC_FP16_TC && fstage_tc_tiles_supported(nch);
+  if (h->tc_tiles) {
+    const int W = 2 * xtc_cpt(S);
+    const size_t nslice = (size_t)(nch + W - 1) / W;
+    const size_t nkt = (size_t)(h->CB + 63) / 64;
+    const size_t bytes = (size_t)G * nslice * nkt * 32768;
+    if ((rc = dalloc(h, (void**)&h->d_tiles, bytes, "operand tiles"))) return rc;
+    // rows beyond the stations of a tile stay zero for good
+    CK(cudaMemset(h->d_tiles, 0, bytes), "operand tiles clear");
+  }
   *h->h_err = 0;
   CK(cudaMemset(h->d_err, 0, sizeof(int)), "error flag reset");
   // W_N^m = exp(-2 pi i m / N), computed in FP64 on the host
@@ -428,7 +444,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
 
   // 2. F and X per chunk
   const int nbl = nbl_of(S);
-  const int kz_used = h->precision == CORR_PREC_FP16_TC ? h->KZ_tc : h->KZ;
+  const int kz_used = h->precision == CORR_PREC_FP16_TC ? (h->tc_tiles ? 1 : h->KZ_tc) : h->KZ;
   CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, h->stream),
      "partials memset");
   const bool tc = h->precision == CORR_PREC_FP16_TC;
@@ -439,6 +455,34 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
       fp.out_kind = 1;
       fp.scale = ldexpf(1.0f, -h->sigma);
     }
+    if (h->tc_tiles) {
+      // F writes MMA operand tiles; X fetches them with bulk copies
+      TcTiles o;
+      o.tiles = h->d_tiles;
+      o.cpt = xtc_cpt(S);
+      o.W = 2 * o.cpt;
+      o.nslice = (h->nchan + o.W - 1) / o.W;
+      o.NKT = (cb + 63) / 64;
+      o.scale = ldexpf(1.0f, -h->sigma);
+      pa = prof_begin(h);
+      CK(launch_fstage_tc(fp, o, h->stream), "tensor-core fstage launch");
+      prof_end(h, 1, pa);
+      XTC2Params xp;
+      xp.tiles = h->d_tiles;
+      xp.nslice = o.nslice;
+      xp.NKT = o.NKT;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.cpt = o.cpt;
+      xp.W = o.W;
+      xp.part = h->d_part;
+      xp.err = h->d_err;
+      pa = prof_begin(h);
+      CK(launch_xtc2(xp, h->sm_count, h->stream), "tensor-core xstage launch");
+      prof_end(h, 2, pa);
+      continue;
+    }
     pa = prof_begin(h);
     CK(launch_fstage(fp, h->stream), "fstage launch");
     prof_end(h, 1, pa);
@@ -447,7 +491,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
       xp.spec = reinterpret_cast<const __half2*>(h->d_spec);
       xp.CB = cb;
       xp.cb = cb;
-      xp.kblocks = 256;
+      xp.kblocks = kTcBlocks;
       xp.S = S;
       xp.G = h->G;
       xp.nchan = h->nchan;

@@ -63,12 +63,29 @@ struct FParams {
   void* out;                // [G][CB][S][nchan]
 };
 
+// MMA operand tiles written by the tensor-core F step: for stream j, channel
+// slice sl (W channels), K range kt (64 blocks) two 16 KB tiles (channel
+// groups of cpt), tile index ((j * nslice + sl) * NKT + kt) * 2 + group.
+struct TcTiles {
+  unsigned char* tiles;
+  int nslice, NKT, W, cpt;
+  float scale;              // exact power of two applied before the FP16 rounding
+};
+
+// X step on tensor cores from operand tiles (see TcTiles).
+struct XTC2Params {
+  const unsigned char* tiles;
+  int nslice, NKT, S, G, nchan, cpt, W;
+  float2* part;             // [G][nchan][nbl]
+  int* err;
+};
+
 // X step on tensor cores: FP16 spectra in, FP32 partial sums out.
 struct XTCParams {
   const __half2* spec;      // [G][CB][S][nchan]
   int CB;                   // blocks per stream in the spectra buffer
   int cb;                   // blocks present in this chunk
-  int kblocks;              // blocks per partial sum (a multiple of 64, <= 256)
+  int kblocks;              // blocks per partial sum (a multiple of 64)
   int S, G, nchan;
   int cpt;                  // channels per 128-row tile (floor(64/S))
   int W;                    // channels per work item (2 * cpt)
@@ -106,6 +123,9 @@ cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
 cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, cudaStream_t s);
 int xtc_cpt(int S);
+bool fstage_tc_tiles_supported(int nchan);
+cudaError_t launch_fstage_tc(const FParams& p, const TcTiles& o, cudaStream_t s);
+cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s);
 size_t xtc_smem_bytes(int S);
 cudaError_t launch_xtc(const XTCParams& p, int sm_count, cudaStream_t s);
 // finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale

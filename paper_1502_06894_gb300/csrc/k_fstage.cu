@@ -364,6 +364,216 @@ k_fstage(FParams p, int slots, int wslot) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core variant of the F step (FFT length N <= 2048): writes the FP16
+// spectra directly as the X step's MMA operand tiles.  A tile holds one
+// stream, one 64-block K range and a group of cpt channels: rows
+// r = (channel-in-group * S + station) * 2 + {0: Re, 1: Im}, 128 rows x 64
+// blocks of FP16, K-major with the 128-byte swizzle (16-byte chunk c of row r
+// stored at chunk c ^ (r % 8)).  Two groups (W = 2 cpt channels) form one
+// 32 KB pair that the X step fetches with a single bulk copy.
+//
+// One CTA takes one station and 8 consecutive blocks (one 16-byte K chunk).
+// Per round its groups transform the 8 blocks of NGRP/8 streams, keep the
+// FP16 spectra in shared memory, then all threads corner-turn them: for each
+// channel and Re/Im the 8 blocks become one 16-byte store.  The packed
+// samples are read straight from global memory (L1-cached across streams).
+
+template <int GC>
+__device__ __forceinline__ void load_pair_g(const StationView& sv, int64_t rel, int G, int m, int j,
+                                            uint32_t& c0, uint32_t& c1) {
+  if constexpr (GC == 16) {
+    const int64_t w = rel + 2 * m;  // one word per sample-time group
+    c0 = (__ldg(&sv.words[w]) >> (2 * j)) & 3u;
+    c1 = (__ldg(&sv.words[w + 1]) >> (2 * j)) & 3u;
+  } else {
+    const int64_t bit = 2 * ((rel + 2 * m) * G + j);
+    c0 = (__ldg(&sv.words[bit >> 5]) >> (bit & 31)) & 3u;
+    const int64_t bit1 = bit + 2 * G;
+    c1 = (__ldg(&sv.words[bit1 >> 5]) >> (bit1 & 31)) & 3u;
+  }
+}
+
+template <int L, int GC>
+__global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)
+k_fstage_tc(FParams p, TcTiles o) {
+  using P = Plan<L>;
+  constexpr int T = P::T;
+  constexpr int NGRP = Groups<L>::NGRP;
+  static_assert(NGRP >= 8 && NGRP % 8 == 0, "the tile writer needs 8 groups per stream");
+  constexpr int SPR = NGRP / 8;  // streams per round
+  constexpr int BUF = kBufPad(L);
+  constexpr int R0 = P::R0;
+  constexpr int PER0 = L / R0 / T;
+  constexpr int HALF = L / 2;
+  constexpr int QN = HALF / T + 1;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int grp = tid / T;
+  const int t = tid - grp * T;
+  float2* fbuf = fbuf_all + grp * BUF;
+  const int s = blockIdx.y;
+  const int G = GC ? GC : p.G;
+  const StationView sv = p.st[s];
+  const int blk = grp & 7;
+  const int bb = blockIdx.x * 8 + blk;  // block within the chunk
+  const bool present = bb < p.CB;
+  const int d = p.blk0 + (present ? bb : 0);
+  const bool valid = present && p.valid[(size_t)s * p.ld + d] != 0;
+  const int64_t rel = valid ? p.start[(size_t)s * p.ld + d] - sv.sample0 : 0;
+  const float delta = valid ? p.delta[(size_t)s * p.ld + d] : 0.f;
+  const float l0 = p.lut0, l1 = p.lut1, l2 = p.lut2, l3 = p.lut3;
+  const int kt = (blockIdx.x * 8) / 64;
+  const int kc = (blockIdx.x & 7);  // 16-byte chunk of the 64-block K range
+
+  for (int r0 = 0; r0 < G; r0 += SPR) {
+    const int j = r0 + grp / 8;
+    const bool ok = valid && j < G;
+    // ---- pass 0 from global memory ----
+    {
+      float2 v[PER0][R0];
+#pragma unroll
+      for (int u = 0; u < PER0; ++u) {
+        const int jj = t + u * T;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) {
+          const int m = jj + r * (L / R0);
+          float x0 = 0.f, x1 = 0.f;
+          if (ok) {
+            uint32_t c0, c1;
+            load_pair_g<GC>(sv, rel, G, m, j, c0, c1);
+            x0 = level(c0, l0, l1, l2, l3);
+            x1 = level(c1, l0, l1, l2, l3);
+          }
+          v[u][r] = make_float2(x0, x1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < PER0; ++u) {
+        const int jj = t + u * T;
+        dft_reg<R0>(v[u]);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) fbuf[pad32(jj * R0 + r)] = v[u][r];
+      }
+      gsync<T>(grp);
+    }
+    if constexpr (P::R1 > 1) stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN);
+    if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
+
+    // ---- real split + rotation into registers, then FP16 into the group's buffer ----
+    const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
+    float2 xa[QN], xb[QN];
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      const int k = t + q * T;
+      xa[q] = make_float2(0.f, 0.f);
+      xb[q] = make_float2(0.f, 0.f);
+      if (ok && k <= HALF) {
+        const int km = (L - k) & (L - 1);
+        const float2 Zk = fbuf[pad32(k)];
+        const float2 Zm = fbuf[pad32(km)];
+        const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
+        const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
+        const float2 w = __ldg(&p.twN[k]);
+        const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
+        float2 Xa = make_float2(E.x + WO.x, E.y + WO.y);
+        float2 Xb = make_float2(E.x - WO.x, WO.y - E.y);
+        float ph = fmaf((float)k, delta, phi);
+        ph -= rintf(ph);
+        float sn, cs;
+        __sincosf(6.28318530717958648f * ph, &sn, &cs);
+        xa[q] = make_float2(Xa.x * cs - Xa.y * sn, Xa.x * sn + Xa.y * cs);
+        float ph2 = fmaf((float)km, delta, phi);
+        ph2 -= rintf(ph2);
+        __sincosf(6.28318530717958648f * ph2, &sn, &cs);
+        xb[q] = make_float2(Xb.x * cs - Xb.y * sn, Xb.x * sn + Xb.y * cs);
+      }
+    }
+    gsync<T>(grp);
+    __half2* xh = reinterpret_cast<__half2*>(fbuf);
+#pragma unroll
+    for (int q = 0; q < QN; ++q) {
+      const int k = t + q * T;
+      if (k <= HALF) {
+        const int km = (L - k) & (L - 1);
+        xh[k] = __floats2half2_rn(xa[q].x * o.scale, xa[q].y * o.scale);
+        if (k != 0 && k != HALF) xh[km] = __floats2half2_rn(xb[q].x * o.scale, xb[q].y * o.scale);
+      }
+    }
+    __syncthreads();
+
+    // ---- corner turn: 8 blocks of (stream, channel, Re/Im) -> one 16-byte chunk ----
+    for (int it = tid; it < SPR * L; it += NGRP * T) {
+      const int ss = it / L;
+      const int k = it - ss * L;
+      const int jo = r0 + ss;
+      if (jo >= G) continue;
+      uint32_t re[4], im[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const __half2 a = reinterpret_cast<const __half2*>(fbuf_all + (ss * 8 + e) * BUF)[k];
+        const __half2 b = reinterpret_cast<const __half2*>(fbuf_all + (ss * 8 + e + 1) * BUF)[k];
+        re[e / 2] = (uint32_t)__half_as_ushort(__low2half(a)) | ((uint32_t)__half_as_ushort(__low2half(b)) << 16);
+        im[e / 2] = (uint32_t)__half_as_ushort(__high2half(a)) | ((uint32_t)__half_as_ushort(__high2half(b)) << 16);
+      }
+      const int sl = k / o.W;
+      const int cw = k - sl * o.W;
+      const int tg = cw / o.cpt;
+      const int cl = cw - tg * o.cpt;
+      const int r = (cl * p.S + s) * 2;
+      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+      *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
+          make_uint4(re[0], re[1], re[2], re[3]);
+      const int r1 = r + 1;
+      *reinterpret_cast<uint4*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4)) =
+          make_uint4(im[0], im[1], im[2], im[3]);
+    }
+    __syncthreads();
+  }
+}
+
+template <int L, int GC>
+static cudaError_t launch_tc_LG(const FParams& p, const TcTiles& o, cudaStream_t st) {
+  constexpr int T = Plan<L>::T;
+  constexpr int NGRP = Groups<L>::NGRP;
+  const size_t smem = (size_t)NGRP * kBufPad(L) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_fstage_tc<L, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(o.NKT * 8, p.S);
+  k_fstage_tc<L, GC><<<grid, T * NGRP, smem, st>>>(p, o);
+  return cudaGetLastError();
+}
+
+template <int L>
+static cudaError_t launch_tc_L(const FParams& p, const TcTiles& o, cudaStream_t st) {
+  if constexpr (Groups<L>::NGRP >= 8 && Groups<L>::NGRP % 8 == 0) {
+    if (p.G == 16) return launch_tc_LG<L, 16>(p, o, st);
+    return launch_tc_LG<L, 0>(p, o, st);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+bool fstage_tc_tiles_supported(int nchan) { return nchan >= 4 && nchan <= 1024; }
+
+cudaError_t launch_fstage_tc(const FParams& p, const TcTiles& o, cudaStream_t s) {
+  if (p.CB <= 0) return cudaSuccess;
+  switch (p.nchan) {
+    case 4: return launch_tc_L<4>(p, o, s);
+    case 8: return launch_tc_L<8>(p, o, s);
+    case 16: return launch_tc_L<16>(p, o, s);
+    case 32: return launch_tc_L<32>(p, o, s);
+    case 64: return launch_tc_L<64>(p, o, s);
+    case 128: return launch_tc_L<128>(p, o, s);
+    case 256: return launch_tc_L<256>(p, o, s);
+    case 512: return launch_tc_L<512>(p, o, s);
+    case 1024: return launch_tc_L<1024>(p, o, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int L, int GC>
 static cudaError_t launch_LG(const FParams& p, cudaStream_t st) {
   constexpr int T = Plan<L>::T;

@@ -17,7 +17,7 @@
 //   of a slice of W = 2*cpt channels
 //   --threads--> two 128 x 64 operand tiles, K-major, 128-byte swizzle
 //   --tcgen05.mma, issued by one thread--> two 128 x 128 FP32 accumulators in
-//   TMEM (256 columns), accumulated over the item's K tiles (<= 256 blocks)
+//   TMEM (256 columns), accumulated over the item's K tiles (<= 1024 blocks)
 //   --tcgen05.ld + lane shuffle (Re/Im rows are neighbouring lanes)-->
 //   V_ab added to an FP32 partial sum in global memory (fixed order).
 // Every wait on an mbarrier is bounded; on timeout the CTA sets *err, stops
@@ -202,12 +202,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
     // ---- transpose staging (natural [b][s][c], half2) -> two swizzled operand tiles ----
     {
       const __half2* st = reinterpret_cast<const __half2*>(stage + (t % kStages) * stage_bytes);
-      const int units = 2 * cpt * S * 8;  // (group, channel, station, 8-block chunk)
+      // unit = (8-block chunk kc, station s, channel gc of the slice), gc fastest
+      // so that a warp's reads of the staging are consecutive words
+      const int units = 2 * cpt * S * 8;
       for (int u = tid; u < units; u += kThreads) {
-        const int kc = u & 7;
-        const int rest = u >> 3;
+        const int gc = u % W;                // group * cpt + channel-in-group
+        const int rest = u / W;
         const int s = rest % S;
-        const int gc = rest / S;             // group * cpt + channel-in-group
+        const int kc = rest / S;
         const int grp = gc / cpt;
         const int cl = gc - grp * cpt;
         uint32_t re[4], im[4];
@@ -258,13 +260,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
       const bool re_lane = ((lane & 1) == 0) && r < rows_valid;
       const int a = (r >> 1) % S;
       const int cl = (r >> 1) / S;
+      // this warp's rows hold channels cmin..cmax of each group: only their
+      // diagonal blocks of the accumulator are read
+      int rlast = warp * 32 + 31;
+      if (rlast > rows_valid - 1) rlast = rows_valid - 1;
+      const int cmin = (warp * 32) / (2 * S), cmax = rlast / (2 * S);
+      const int q0 = (2 * S * cmin) / 32, q1 = (warp * 32 < rows_valid) ? (2 * S * (cmax + 1) - 1) / 32 : -1;
 #pragma unroll 1
       for (int grp = 0; grp < 2; ++grp) {
         const int k = c0 + grp * cpt + cl;
         float2* dst = p.part + (((size_t)kz * G + g) * nchan + (k < nchan ? k : 0)) * nbl;
         const bool mine = re_lane && k < nchan;
 #pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
+        for (int q = q0; q <= q1; ++q) {
           uint32_t v[32];
           tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + grp * 128 + q * 32, v);
 #pragma unroll
@@ -298,6 +306,185 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(taddr));
+}
+
+// ---------------------------------------------------------------------------
+// k_xmma2: the X step from ready-made operand tiles (written by the tensor-core
+// F step), in the warp-specialised form of a Blackwell GEMM:
+//   warp 4, lane 0  producer + MMA issuer: one 32 KB cp.async.bulk per K tile
+//                   into a 4-stage ring (mbarrier with transaction count), then
+//                   8 MMAs (2 channel groups x 4 K steps) into one of two
+//                   256-column TMEM accumulators, tcgen05.commit to free the
+//                   stage / publish the accumulator;
+//   warps 0-3       epilogue: TMEM -> registers, Re/Im lane shuffle, V_ab into
+//                   the partial sums, then release the accumulator.
+// Every wait is bounded; a timeout sets *err and makes all roles stop.
+namespace {
+
+constexpr int kStages2 = 4;
+constexpr int kPairBytes = 2 * kTileBytes;  // two channel-group tiles per K tile
+
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  uint32_t ok = 0;
+  for (long it = 0; it < kWaitLimit; ++it) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  unsigned char* ring = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // [kStages2][32 KB]
+  __shared__ __align__(8) uint64_t s_full[kStages2], s_empty[kStages2], s_acc_full[2], s_acc_empty[2];
+  __shared__ uint32_t s_taddr;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = p.S, cpt = p.cpt, W = p.W, G = p.G, nchan = p.nchan, NKT = p.NKT;
+  const int nbl = nbl_of(S);
+  const int rows_valid = 2 * S * cpt;
+
+  if (tid == 0) {
+    for (int i = 0; i < kStages2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[i])));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_acc_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&s_acc_empty[i])));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&s_taddr)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = s_taddr;
+
+  // items of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; each has NKT K tiles
+  const int my_items = nitems > (int)blockIdx.x ? (nitems - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int my_tiles = my_items * NKT;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      auto load = [&](int u) {
+        const int n = u / NKT, kt = u - n * NKT;
+        const int item = blockIdx.x + n * gridDim.x;  // = g * nslice + sl
+        const int st = u % kStages2;
+        const unsigned char* src = p.tiles + ((size_t)item * NKT + kt) * kPairBytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_full[st])),
+                     "r"(kPairBytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(ring + st * kPairBytes)),
+            "l"(src), "r"(kPairBytes), "r"(smem_u32(&s_full[st]))
+            : "memory");
+      };
+      for (int u = 0; u < kStages2 && u < my_tiles; ++u) load(u);
+      for (int u = 0; u < my_tiles && !s_abort; ++u) {
+        const int n = u / NKT, kt = u - n * NKT;
+        const int st = u % kStages2;
+        const int ab = n & 1;
+        if (!mbar_wait_abort(&s_full[st], (u / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
+        if (kt == 0 && n >= 2 && !mbar_wait_abort(&s_acc_empty[ab], ((n - 2) >> 1) & 1, &s_abort)) {
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int grp = 0; grp < 2; ++grp) {
+          const uint64_t d0 = sw128_desc(smem_u32(ring + st * kPairBytes + grp * kTileBytes));
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            mma_f16(taddr + ab * 256 + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (kt > 0 || ks > 0) ? 1u : 0u);
+        }
+        mma_commit(&s_empty[st]);
+        if (kt == NKT - 1) mma_commit(&s_acc_full[ab]);
+        const int nxt = u + kStages2;
+        if (nxt < my_tiles) {
+          if (!mbar_wait_abort(&s_empty[st], (u / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
+          load(nxt);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue warps 0..3: TMEM lane quadrant = warp ----
+    const int r = warp * 32 + lane;
+    const bool re_lane = ((lane & 1) == 0) && r < rows_valid;
+    const int a = (r >> 1) % S;
+    const int cl = (r >> 1) / S;
+    int rlast = warp * 32 + 31;
+    if (rlast > rows_valid - 1) rlast = rows_valid - 1;
+    const int cmin = (warp * 32) / (2 * S), cmax = rlast / (2 * S);
+    const int q0 = (2 * S * cmin) / 32, q1 = (warp * 32 < rows_valid) ? (2 * S * (cmax + 1) - 1) / 32 : -1;
+    for (int n = 0; n < my_items; ++n) {
+      const int ab = n & 1;
+      if (!mbar_wait_abort(&s_acc_full[ab], (n >> 1) & 1, &s_abort)) { s_abort = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int item = blockIdx.x + n * gridDim.x;
+      const int g = item / p.nslice;
+      const int c0 = (item - g * p.nslice) * W;
+#pragma unroll 1
+      for (int grp = 0; grp < 2; ++grp) {
+        const int k = c0 + grp * cpt + cl;
+        float2* dst = p.part + ((size_t)g * nchan + (k < nchan ? k : 0)) * nbl;
+        const bool mine = re_lane && k < nchan;
+#pragma unroll 1
+        for (int q = q0; q <= q1; ++q) {
+          uint32_t v[32];
+          tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + ab * 256 + grp * 128 + q * 32, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float m0 = __uint_as_float(v[2 * i]), m1 = __uint_as_float(v[2 * i + 1]);
+            const float n0 = __shfl_down_sync(0xffffffffu, m0, 1);
+            const float n1 = __shfl_down_sync(0xffffffffu, m1, 1);
+            const int j = q * 32 + 2 * i;
+            const int clj = (j >> 1) / S;
+            const int b = (j >> 1) % S;
+            if (mine && clj == cl && b >= a) {
+              float2* o = dst + bl_index(a, b, S);
+              float2 x = *o;
+              x.x += m0 + n1;
+              x.y += n0 - m1;
+              *o = x;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_acc_empty[ab])) : "memory");
+    }
+  }
+
+  __syncthreads();
+  if (tid == 0 && s_abort) atomicExch(p.err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
+}
+
+cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
+  const int nitems = p.G * p.nslice;
+  if (nitems <= 0 || p.NKT <= 0) return cudaSuccess;
+  const size_t smem = 1024 + (size_t)kStages2 * kPairBytes;
+  cudaError_t e = cudaFuncSetAttribute(k_xmma2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = nitems < sm_count ? nitems : sm_count;
+  k_xmma2<<<grid, 160, smem, s>>>(p, nitems);
+  return cudaGetLastError();
 }
 
 int xtc_cpt(int S) { return S <= 64 ? 64 / S : 0; }

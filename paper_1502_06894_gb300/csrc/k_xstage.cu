@@ -84,6 +84,101 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     }
 }
 
+// For S <= 12 (one triangular tile of baselines per channel) the spectra
+// reach the threads through a shared-memory ring filled by cp.async, so the
+// number of bytes in flight no longer depends on how many registers the
+// accumulators take: kStagesX stages of kNB blocks x S stations x 128
+// channels, one CTA per (128-channel tile, stream, block range).
+constexpr int kNB = 2;       // blocks per stage
+constexpr int kStagesX = 4;  // ring depth
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+
+template <int TA>
+__global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  float2* ring = reinterpret_cast<float2*>(xs_raw);  // [kStagesX][kNB][S][kXT]
+  const int tid = threadIdx.x;
+  const int k0 = blockIdx.x * kXT;
+  const int k = k0 + tid;
+  const int g = blockIdx.y;
+  const int kz = blockIdx.z;
+  const int S = p.S;
+  const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
+  const int b_hi = (int)((int64_t)p.CB * (kz + 1) / p.KZ);
+  if (b_hi <= b_lo) return;
+  const int nst = (b_hi - b_lo + kNB - 1) / kNB;  // stages of this CTA
+  const int stage_elems = kNB * S * kXT;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+
+  // issue the copies of stage q (blocks b_lo + q*kNB ...) into ring slot q % kStagesX
+  auto issue = [&](int q) {
+    if (q < nst) {
+      const int slot = q % kStagesX;
+      const int chunks = kNB * S * (kXT * 8 / 16);  // 16-byte pieces
+      for (int c = tid; c < chunks; c += kXT) {
+        const int row = c >> 6;                    // (block-in-stage, station), 64 pieces per row
+        const int piece = c & 63;
+        const int bi = row / S;
+        const int st = row - bi * S;
+        const int b = b_lo + q * kNB + bi;
+        const int ch = k0 + piece * 2;
+        const bool in = b < b_hi && ch < p.nchan;
+        const float2* src = p.spec + ((size_t)g * p.CB + (in ? b : b_lo)) * (size_t)S * p.nchan +
+                            (size_t)st * p.nchan + (in ? ch : 0);
+        const uint32_t dst = ring_s + (uint32_t)(((slot * kNB + bi) * S + st) * kXT + piece * 2) * 8u;
+        cp_async16(dst, src, in ? 16 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  float2 acc[TA][TA];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+#pragma unroll
+  for (int q = 0; q < kStagesX - 1; ++q) issue(q);
+  for (int q = 0; q < nst; ++q) {
+    issue(q + kStagesX - 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kStagesX - 1) : "memory");
+    __syncthreads();
+    const float2* st = ring + (q % kStagesX) * stage_elems;
+#pragma unroll
+    for (int bi = 0; bi < kNB; ++bi) {
+      float2 a[TA];
+#pragma unroll
+      for (int i = 0; i < TA; ++i) a[i] = i < S ? st[(bi * S + i) * kXT + tid] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < TA; ++i)
+#pragma unroll
+        for (int j = i; j < TA; ++j) {
+          acc[i][j].x = fmaf(a[i].x, a[j].x, fmaf(a[i].y, a[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].y, a[j].x, fmaf(-a[i].x, a[j].y, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (k >= p.nchan) return;
+  const int nbl = nbl_of(S);
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = i; j < TA; ++j)
+      if (i < S && j < S) {
+        float2* dst = p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) * (size_t)p.nchan + k;
+        float2 v = *dst;
+        v.x += acc[i][j].x;
+        v.y += acc[i][j].y;
+        *dst = v;
+      }
+}
+
 static int tile_for(int S) {
   if (S <= 2) return 2;
   if (S <= 4) return 4;
@@ -98,12 +193,23 @@ int xstage_kz(int CB, int S, int G, int nchan) {
   const int TA = tile_for(S);
   const int nt = (S + TA - 1) / TA;
   const long ctas = (long)((nchan + kXT - 1) / kXT) * G * (nt * (nt + 1) / 2);
-  int kz = (int)((4L * 152 + ctas - 1) / ctas);  // at least ~4 CTAs per SM
+  // about three waves of two CTAs per SM
+  int kz = (int)((3L * 2 * 152 + ctas - 1) / ctas);
   const int by256 = (CB + 255) / 256;            // each partial sums <= 256 blocks
   if (kz < by256) kz = by256;
   if (kz > CB) kz = CB;
   if (kz < 1) kz = 1;
   return kz;
+}
+
+template <int TA>
+static cudaError_t launch_ring(const XParams& p, cudaStream_t s) {
+  const size_t smem = (size_t)kStagesX * kNB * p.S * kXT * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_xmac_ring<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.nchan + kXT - 1) / kXT, p.G, p.KZ);
+  k_xmac_ring<TA><<<grid, kXT, smem, s>>>(p);
+  return cudaGetLastError();
 }
 
 template <int TA>
@@ -124,12 +230,12 @@ static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
 cudaError_t launch_xstage(const XParams& p, cudaStream_t s) {
   if (p.CB <= 0) return cudaSuccess;
   switch (tile_for(p.S)) {
-    case 2: return launch_TA<2>(p, s);
-    case 4: return launch_TA<4>(p, s);
-    case 6: return launch_TA<6>(p, s);
-    case 8: return launch_TA<8>(p, s);
-    case 10: return launch_TA<10>(p, s);
-    case 12: return launch_TA<12>(p, s);
+    case 2: return launch_ring<2>(p, s);
+    case 4: return launch_ring<4>(p, s);
+    case 6: return launch_ring<6>(p, s);
+    case 8: return p.S <= 8 ? launch_ring<8>(p, s) : launch_TA<8>(p, s);
+    case 10: return launch_ring<10>(p, s);
+    case 12: return launch_ring<12>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }
