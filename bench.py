@@ -72,6 +72,19 @@ def dist_env():
     return ws, rank, local
 
 
+def traffic_per_launch(kernel):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary table (captured at the benchmark's launch shape), else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel:
+            return float(parts[1])
+    return None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -341,7 +354,12 @@ def main():
     else:
         roof = {"bound": "alu", "achieved": tfl, "peak": peak_alu / 1e12, "unit": "TFLOP/s", "frac": alu_frac,
                 "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
-    roof.update({"kernel": "k_fstage<1024>" if dom == "fstage" else "k_xmac<10>",
+    gc = G if G in (16, 32) else 0
+    kname = "k_fstage<%d,%d>" % (nch, gc) if dom == "fstage" else "k_xmac_ring<%d>" % S
+    traffic = traffic_per_launch(kname)
+    roof["traffic"] = traffic
+    roof["traffic_over_algorithmic"] = (traffic / (d_bytes / max(d_n, 1))) if traffic else None
+    roof.update({"kernel": kname,
                  "bytes_per_launch": d_bytes / max(d_n, 1), "flops_per_launch": d_flops / max(d_n, 1),
                  "launch_ms": t_launch * 1e3, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
     launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
@@ -374,15 +392,41 @@ def main():
         out_h = torch.empty((nint, nbl, G, nch), dtype=torch.complex64, pin_memory=True)
         w_h = torch.empty((nint, nbl), dtype=torch.float64, pin_memory=True)
 
+        # each station's pinned bytes in nint pieces (whole 32-bit words);
+        # pieces are pushed two integrations ahead with corr_push_samples_async,
+        # so host->device copies overlap the correlation of earlier integrations
+        pieces = []
+        for s in range(S):
+            nb = host[s].numel()
+            cuts = [((nb * k) // nint) // 4 * 4 for k in range(nint)] + [nb]
+            pieces.append([host[s][cuts[k]:cuts[k + 1]] for k in range(nint)])
+
         def e2e_step():
             c2.reset()
-            for s in range(S):
-                c2.push(s, host[s])
-            c2.flush()
+            pushed = 0
+
+            def push_next():
+                nonlocal pushed
+                if pushed < nint:
+                    for s in range(S):
+                        c2.push_async(s, pieces[s][pushed])
+                    pushed += 1
+                    if pushed == nint:
+                        c2.flush()
+                    return True
+                return False
+
+            push_next()
+            push_next()
             for i in range(nint):
-                rc = c2.correlate_into(out_h[i], w_h[i])
-                if rc != corr.CORR_OK:
-                    raise RuntimeError("corr_correlate returned %d" % rc)
+                push_next()
+                while True:
+                    rc = c2.correlate_into(out_h[i], w_h[i])
+                    if rc == corr.CORR_OK:
+                        break
+                    if rc != corr.CORR_EAGAIN or not push_next():
+                        raise RuntimeError("corr_correlate returned %d" % rc)
+            c2.wait_pushes()
 
         e2e_step()
         torch.cuda.synchronize()

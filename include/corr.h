@@ -124,6 +124,20 @@ int corr_reserve(corr_t *h, int station, size_t nbytes);
  * so the caller may reuse the buffer; pinned host memory copies fastest. */
 int corr_push_samples(corr_t *h, int station, const void *bytes, size_t nbytes);
 
+/* Append packed bytes without waiting for the copy: the copy runs on the
+ * handle's copy streams and overlaps correlation; a later corr_correlate*
+ * call makes its device work wait for the pushed pieces it reads.  bytes
+ * should be pinned host memory (pageable memory works but copies without
+ * overlap) and must stay unchanged until corr_wait_pushes returns (or the
+ * handle is reset or destroyed).  nbytes must be a multiple of 4.  Growing
+ * the station's device buffer (push beyond corr_reserve) waits for earlier
+ * copies first. */
+int corr_push_samples_async(corr_t *h, int station, const void *bytes, size_t nbytes);
+
+/* Wait until every asynchronous push of the handle has landed in device
+ * memory (the host buffers may then be reused). */
+int corr_wait_pushes(corr_t *h);
+
 /* Use nbytes of packed samples that already live in device memory of the
  * handle's device (16-byte aligned, nbytes a multiple of 4) as the station's
  * whole stream.  The caller keeps ownership and must keep the memory alive

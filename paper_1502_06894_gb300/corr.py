@@ -59,6 +59,8 @@ _SIGS = {
     "corr_set_stream_start": ([_H, C.c_int, C.c_int64], C.c_int),
     "corr_reserve": ([_H, C.c_int, C.c_size_t], C.c_int),
     "corr_push_samples": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
+    "corr_push_samples_async": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
+    "corr_wait_pushes": ([_H], C.c_int),
     "corr_attach_samples_device": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
     "corr_flush": ([_H], C.c_int),
     "corr_correlate": ([_H, _P, _P], C.c_int),
@@ -174,6 +176,20 @@ class Correlator:
         else:
             n = data.numel() * data.element_size()
         self._check(corr_push_samples(self.h, station, _ptr(data), n))
+
+    def push_async(self, station: int, data):
+        """Append pinned host bytes without waiting; keep `data` unchanged (and
+        alive) until wait_pushes()."""
+        if isinstance(data, np.ndarray):
+            n = data.nbytes
+        else:
+            n = data.numel() * data.element_size()
+        self._keep.append(data)
+        self._check(corr_push_samples_async(self.h, station, _ptr(data), n))
+
+    def wait_pushes(self):
+        self._check(corr_wait_pushes(self.h))
+        self._keep = [k for k in self._keep if hasattr(k, "is_cuda") and k.is_cuda]
 
     def attach_device(self, station: int, dev_tensor):
         """Use a CUDA tensor's bytes as the station's whole stream (kept alive here)."""

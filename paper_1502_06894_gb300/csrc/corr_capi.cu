@@ -38,7 +38,17 @@ struct Station {
   int64_t sample0 = 0;
   bool started = false;     // a push or attach happened
   std::vector<Seg> segs;
+  // asynchronous pushes not yet waited for by the compute stream: the byte
+  // range of each piece and the event recorded after its copy
+  struct Piece {
+    size_t start, end;
+    cudaEvent_t ev;
+  };
+  std::vector<Piece> pending;
 };
+
+constexpr int kCopyStreams = 2;             // copies alternate between these
+constexpr size_t kCopyPiece = (size_t)64 << 20;  // large pushes split into pieces
 
 bool g_const_ready[64];
 std::mutex g_const_mu;
@@ -54,6 +64,8 @@ struct corr_s {
   std::vector<double> nu0;
   int precision = CORR_PREC_FP32;
   cudaStream_t own_stream = nullptr;
+  cudaStream_t copy_stream[kCopyStreams] = {nullptr, nullptr};
+  int copy_next = 0;
   cudaStream_t stream = nullptr;
   std::vector<Station> st;
   bool flushed = false;
@@ -179,6 +191,13 @@ static int prof_collect(corr_t* h) {
     h->ev_pool.push_back(m.b);
   }
   h->marks.clear();
+  return CORR_OK;
+}
+
+// All asynchronous copies done (host buffers reusable); compute stream not involved.
+static int drain_pushes(corr_t* h) {
+  for (int q = 0; q < kCopyStreams; ++q)
+    if (h->copy_stream[q]) CK(cudaStreamSynchronize(h->copy_stream[q]), "wait for pushes");
   return CORR_OK;
 }
 
@@ -430,6 +449,24 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   CK(cudaStreamSynchronize(h->stream), "delay_blocks");
   if (*h->h_err) return h->fail(CORR_ETIMEOUT, "a tensor-core X-step wait timed out on the device");
   const unsigned long long off = 1ull << 62;
+  // the compute stream waits for the asynchronous pushes holding the bytes
+  // this integration reads (pieces that start below the last byte needed)
+  for (int s = 0; s < S; ++s) {
+    Station& x = h->st[s];
+    if (x.pending.empty()) continue;
+    const int64_t need = (int64_t)(h->h_stat[3 * s + 0] - off);
+    const size_t need_bytes = need > 0 ? (size_t)((need * (int64_t)h->G * 2 + 7) / 8) : 0;
+    size_t keep = 0;
+    for (size_t q = 0; q < x.pending.size(); ++q) {
+      if (x.pending[q].start < need_bytes || h->flushed) {
+        CK(cudaStreamWaitEvent(h->stream, x.pending[q].ev, 0), "wait for pushed samples");
+        cudaEventDestroy(x.pending[q].ev);
+      } else {
+        x.pending[keep++] = x.pending[q];
+      }
+    }
+    x.pending.resize(keep);
+  }
   bool any_data = false;
   for (int s = 0; s < S; ++s) {
     const int64_t need = (int64_t)(h->h_stat[3 * s + 0] - off);
@@ -586,6 +623,8 @@ int corr_create(corr_t** hp, int stations, int subbands, int pols, int nchan, do
   h->st.resize(stations);
   cudaError_t e = cudaGetDevice(&h->dev);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+  for (int q = 0; q < kCopyStreams && e == cudaSuccess; ++q)
+    e = cudaStreamCreateWithFlags(&h->copy_stream[q], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     g_create_error = std::string("corr_create: ") + cudaGetErrorString(e);
     cudaGetLastError();
@@ -715,6 +754,7 @@ int corr_push_samples(corr_t* h, int station, const void* bytes, size_t nbytes) 
   if (h->flushed) return h->fail(CORR_ESTATE, "corr_push_samples: after corr_flush");
   int rc = use_device(h);
   if (rc) return rc;
+  if (!s.pending.empty() && (rc = drain_pushes(h))) return rc;
   if ((rc = grow(h, s, s.len + nbytes))) return rc;
   if (nbytes) {
     CK(cudaMemcpyAsync(s.dbuf + s.len, bytes, nbytes, cudaMemcpyHostToDevice, h->stream), "push H2D");
@@ -723,6 +763,48 @@ int corr_push_samples(corr_t* h, int station, const void* bytes, size_t nbytes) 
   s.len += nbytes;
   s.started = true;
   return CORR_OK;
+}
+
+int corr_push_samples_async(corr_t* h, int station, const void* bytes, size_t nbytes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_push_samples_async: station out of range");
+  if (nbytes % 4) return h->fail(CORR_EINVAL, "corr_push_samples_async: nbytes must be a multiple of 4");
+  if (nbytes && !bytes) return h->fail(CORR_EINVAL, "corr_push_samples_async: bytes is NULL");
+  Station& s = h->st[station];
+  if (s.attached) return h->fail(CORR_ESTATE, "corr_push_samples_async: station uses attached device memory");
+  if (h->flushed) return h->fail(CORR_ESTATE, "corr_push_samples_async: after corr_flush");
+  int rc = use_device(h);
+  if (rc) return rc;
+  if (s.len + nbytes > s.cap) {
+    // growing moves the buffer: let every copy into it finish first
+    if ((rc = drain_pushes(h))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync before stream growth");
+    if ((rc = grow(h, s, s.len + nbytes))) return rc;
+  }
+  for (size_t o = 0; o < nbytes; o += kCopyPiece) {
+    const size_t n = nbytes - o < kCopyPiece ? nbytes - o : kCopyPiece;
+    cudaStream_t cs = h->copy_stream[h->copy_next];
+    h->copy_next = (h->copy_next + 1) % kCopyStreams;
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "push event");
+    cudaError_t e = cudaMemcpyAsync(s.dbuf + s.len + o, (const uint8_t*)bytes + o, n, cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(ev);
+      return h->cuda_fail(e, "asynchronous push");
+    }
+    s.pending.push_back({s.len + o, s.len + o + n, ev});
+  }
+  s.len += nbytes;
+  s.started = true;
+  return CORR_OK;
+}
+
+int corr_wait_pushes(corr_t* h) {
+  if (!h) return CORR_EINVAL;
+  int rc = use_device(h);
+  if (rc) return rc;
+  return drain_pushes(h);
 }
 
 int corr_attach_samples_device(corr_t* h, int station, const void* dev_bytes, size_t nbytes) {
@@ -800,7 +882,10 @@ int corr_reset(corr_t* h) {
   int rc = use_device(h);
   if (rc) return rc;
   cudaStreamSynchronize(h->stream);
+  drain_pushes(h);
   for (Station& s : h->st) {
+    for (auto& pe : s.pending) cudaEventDestroy(pe.ev);
+    s.pending.clear();
     if (s.attached) {
       s.ext = nullptr;
       s.attached = false;
@@ -826,7 +911,11 @@ void corr_destroy(corr_t* h) {
   cudaGetDevice(&cur);
   if (cur != h->dev) cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
-  for (Station& s : h->st) cudaFree(s.dbuf);
+  drain_pushes(h);
+  for (Station& s : h->st) {
+    for (auto& pe : s.pending) cudaEventDestroy(pe.ev);
+    cudaFree(s.dbuf);
+  }
   for (auto& m : h->marks) {
     cudaEventDestroy(m.a);
     cudaEventDestroy(m.b);
@@ -834,6 +923,8 @@ void corr_destroy(corr_t* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_device(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  for (int q = 0; q < kCopyStreams; ++q)
+    if (h->copy_stream[q]) cudaStreamDestroy(h->copy_stream[q]);
   if (cur != h->dev && cur >= 0) cudaSetDevice(cur);
   delete h;
 }

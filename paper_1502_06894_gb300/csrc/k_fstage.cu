@@ -6,8 +6,9 @@
 // memory once (all G streams of a station share one window), then each
 // FFT group of T threads transforms one stream:
 //
-//   unpack   2-bit code -> level (4-entry table), two real samples per complex
-//            point, decoded straight into the registers of the first pass;
+//   unpack   2-bit codes -> levels, two real samples per complex point through
+//            one 16-entry table of level pairs (pre-halved, which absorbs the
+//            split's 1/2), decoded straight into the registers of the first pass;
 //   FFT      N real samples as an N/2-point complex FFT (even samples in the
 //            real part, odd in the imaginary part), Stockham auto-sort passes
 //            of radix 8/16/32 held in registers, shared memory between passes
@@ -92,17 +93,12 @@ __device__ __forceinline__ void gsync(int grp) {
   }
 }
 
-__device__ __forceinline__ float level(uint32_t c, float l0, float l1, float l2, float l3) {
-  const float lo = (c & 1u) ? l1 : l0;
-  const float hi = (c & 1u) ? l3 : l2;
-  return (c & 2u) ? hi : lo;
-}
-
 // A later Stockham pass: read R points per butterfly group, twiddle, DFT,
 // write back in place (all reads of the group finish before any write).
 template <int L, int R, int NS, int T>
 __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, int grp,
-                                              const float2* __restrict__ twN) {
+                                              const float2* __restrict__ twN,
+                                              const float2* __restrict__ s_twl = nullptr) {
   constexpr int GROUPS = L / R;
   constexpr int PER = GROUPS / T;
   static_assert(PER >= 1 && GROUPS % T == 0, "bad FFT plan");
@@ -120,8 +116,9 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
     const int k = j & (NS - 1);
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{2 k r L/(NS R)}
-      const float2 w = __ldg(&twN[2 * k * r * (L / (NS * R))]);
+      // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{2 k r L/(NS R)}; for the last
+      // pass (NS R = L) from the shared table s_twl[r NS + k] when given
+      const float2 w = (NS * R == L && s_twl) ? s_twl[r * NS + k] : __ldg(&twN[2 * k * r * (L / (NS * R))]);
       v[u][r] = cmul(v[u][r], w);
     }
     dft_reg<R>(v[u]);
@@ -153,6 +150,37 @@ template <int L> struct Groups {
 };
 
 constexpr int kBufPad(int L) { return L + L / 32 + 1; }
+
+// Shared tables for N <= 2048: the last Stockham pass's twiddles W_L^{k r}
+// (L entries, [r][k]) and the real-split twiddles W_N^k for k <= L/2.
+template <int L> struct Tw {
+  static constexpr bool on = L >= 64 && L <= 1024;
+  static constexpr int size = on ? L + L / 2 + 1 : 1;
+};
+
+// Fill the shared tables: s_lut16[c0 | c1 << 2] = (l[c0], l[c1]) / 2 (the
+// halving takes the 1/2 of the real-FFT split into the input, exactly), and,
+// when Tw<L>::on, the twiddle tables (last pass: NS = L / R_last).
+template <int L, int RLAST>
+__device__ __forceinline__ void fill_tables(float2* s_lut16, float2* s_tw, const FParams& p) {
+  const int tid = threadIdx.x;
+  if (tid < 16) {
+    const float l[4] = {p.lut0, p.lut1, p.lut2, p.lut3};
+    s_lut16[tid] = make_float2(0.5f * l[tid & 3], 0.5f * l[tid >> 2]);
+  }
+  if constexpr (Tw<L>::on) {
+    constexpr int NS = L / RLAST;
+    for (int e = tid; e < L; e += blockDim.x) {
+      const int r = e / NS, k = e - r * NS;
+      s_tw[e] = __ldg(&p.twN[2 * k * r]);
+    }
+    for (int k = tid; k <= L / 2; k += blockDim.x) s_tw[L + k] = __ldg(&p.twN[k]);
+  }
+}
+
+template <int L> struct LastRadix {
+  static constexpr int v = Plan<L>::R2 > 1 ? Plan<L>::R2 : (Plan<L>::R1 > 1 ? Plan<L>::R1 : Plan<L>::R0);
+};
 
 // Byte offset of the packed-word staging area after the NGRP FFT buffers,
 // rounded up to 16 bytes for the 16-byte shared-memory stores.
@@ -228,6 +256,9 @@ k_fstage(FParams p, int slots, int wslot) {
 
   __shared__ int s_boff[64];
   __shared__ int s_ok[64];
+  __shared__ float2 s_lut16[16];
+  __shared__ float2 s_tw[Tw<L>::size];
+  fill_tables<L, LastRadix<L>::v>(s_lut16, s_tw, p);
 
   // ---- stage the windows of this CTA's blocks (16-byte loads where the
   //      words lie inside the station's data, single words at its end) ----
@@ -267,7 +298,6 @@ k_fstage(FParams p, int slots, int wslot) {
   }
   __syncthreads();
 
-  const float l0 = p.lut0, l1 = p.lut1, l2 = p.lut2, l3 = p.lut3;
   const int ntasks = nslots * G;
   for (int base = 0; base < ntasks; base += NGRP) {
     const int task = base + grp;
@@ -290,14 +320,13 @@ k_fstage(FParams p, int slots, int wslot) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int m = jj + r * (L / R0);
-          float x0 = 0.f, x1 = 0.f;
+          float2 xv = make_float2(0.f, 0.f);
           if (ok) {
             uint32_t c0, c1;
             load_pair<GC>(wsl, boff, G, m, j, even, c0, c1);
-            x0 = level(c0, l0, l1, l2, l3);
-            x1 = level(c1, l0, l1, l2, l3);
+            xv = s_lut16[c0 | (c1 << 2)];
           }
-          v[u][r] = make_float2(x0, x1);
+          v[u][r] = xv;
         }
       }
 #pragma unroll
@@ -309,7 +338,8 @@ k_fstage(FParams p, int slots, int wslot) {
       }
       gsync<T>(grp);
     }
-    if constexpr (P::R1 > 1) stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN);
+    if constexpr (P::R1 > 1)
+      stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
     if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
 
     // ---- real split, rotation, store ----
@@ -330,11 +360,13 @@ k_fstage(FParams p, int slots, int wslot) {
         float2 Xa = make_float2(0.f, 0.f), Xb = make_float2(0.f, 0.f);
         const int km = (L - k) & (L - 1);
         if (ok) {
+          // Z is the transform of the halved samples, so E = Z[k] + conj Z[L-k]
+          // and O = -i (Z[k] - conj Z[L-k]) carry the split's factor 1/2
           const float2 Zk = fbuf[pad32(k)];
           const float2 Zm = fbuf[pad32(km)];
-          const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
-          const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
-          const float2 w = __ldg(&p.twN[k]);
+          const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
+          const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
+          const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&p.twN[k]);
           const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
           Xa = make_float2(E.x + WO.x, E.y + WO.y);
           Xb = make_float2(E.x - WO.x, WO.y - E.y);
@@ -410,6 +442,10 @@ k_fstage_tc(FParams p, TcTiles o) {
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
+  __shared__ float2 s_lut16[16];
+  __shared__ float2 s_tw[Tw<L>::size];
+  fill_tables<L, LastRadix<L>::v>(s_lut16, s_tw, p);
+  __syncthreads();
   const int tid = threadIdx.x;
   const int grp = tid / T;
   const int t = tid - grp * T;
@@ -424,7 +460,6 @@ k_fstage_tc(FParams p, TcTiles o) {
   const bool valid = present && p.valid[(size_t)s * p.ld + d] != 0;
   const int64_t rel = valid ? p.start[(size_t)s * p.ld + d] - sv.sample0 : 0;
   const float delta = valid ? p.delta[(size_t)s * p.ld + d] : 0.f;
-  const float l0 = p.lut0, l1 = p.lut1, l2 = p.lut2, l3 = p.lut3;
   const int kt = (blockIdx.x * 8) / 64;
   const int kc = (blockIdx.x & 7);  // 16-byte chunk of the 64-block K range
 
@@ -440,14 +475,13 @@ k_fstage_tc(FParams p, TcTiles o) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int m = jj + r * (L / R0);
-          float x0 = 0.f, x1 = 0.f;
+          float2 xv = make_float2(0.f, 0.f);
           if (ok) {
             uint32_t c0, c1;
             load_pair_g<GC>(sv, rel, G, m, j, c0, c1);
-            x0 = level(c0, l0, l1, l2, l3);
-            x1 = level(c1, l0, l1, l2, l3);
+            xv = s_lut16[c0 | (c1 << 2)];
           }
-          v[u][r] = make_float2(x0, x1);
+          v[u][r] = xv;
         }
       }
 #pragma unroll
@@ -459,7 +493,8 @@ k_fstage_tc(FParams p, TcTiles o) {
       }
       gsync<T>(grp);
     }
-    if constexpr (P::R1 > 1) stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN);
+    if constexpr (P::R1 > 1)
+      stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
     if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
 
     // ---- real split + rotation into registers, then FP16 into the group's buffer ----
@@ -474,9 +509,9 @@ k_fstage_tc(FParams p, TcTiles o) {
         const int km = (L - k) & (L - 1);
         const float2 Zk = fbuf[pad32(k)];
         const float2 Zm = fbuf[pad32(km)];
-        const float2 E = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y - Zm.y));
-        const float2 O = make_float2(0.5f * (Zk.y + Zm.y), -0.5f * (Zk.x - Zm.x));
-        const float2 w = __ldg(&p.twN[k]);
+        const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
+        const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
+        const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&p.twN[k]);
         const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
         float2 Xa = make_float2(E.x + WO.x, E.y + WO.y);
         float2 Xb = make_float2(E.x - WO.x, WO.y - E.y);

@@ -284,11 +284,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
             const int clj = (j >> 1) / S;
             const int b = (j >> 1) % S;
             if (mine && clj == cl && b >= a) {
-              float2* o = dst + bl_index(a, b, S);
-              float2 x = *o;
-              x.x += m0 + n1;
-              x.y += n0 - m1;
-              *o = x;
+              // each partial-sum element gets exactly one add per launch, so a
+              // fire-and-forget reduction keeps the sums deterministic
+              float* o = reinterpret_cast<float*>(dst + bl_index(a, b, S));
+              atomicAdd(o, m0 + n1);
+              atomicAdd(o + 1, n0 - m1);
             }
           }
         }
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
 // k_xmma2: the X step from ready-made operand tiles (written by the tensor-core
 // F step), in the warp-specialised form of a Blackwell GEMM:
 //   warp 4, lane 0  producer + MMA issuer: one 32 KB cp.async.bulk per K tile
-//                   into a 4-stage ring (mbarrier with transaction count), then
+//                   into a 6-stage ring (mbarrier with transaction count), then
 //                   8 MMAs (2 channel groups x 4 K steps) into one of two
 //                   256-column TMEM accumulators, tcgen05.commit to free the
 //                   stage / publish the accumulator;
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, i
 // Every wait is bounded; a timeout sets *err and makes all roles stop.
 namespace {
 
-constexpr int kStages2 = 4;
+constexpr int kStages2 = 6;
 constexpr int kPairBytes = 2 * kTileBytes;  // two channel-group tiles per K tile
 
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
@@ -414,10 +414,15 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
         }
         mma_commit(&s_empty[st]);
         if (kt == NKT - 1) mma_commit(&s_acc_full[ab]);
-        const int nxt = u + kStages2;
-        if (nxt < my_tiles) {
-          if (!mbar_wait_abort(&s_empty[st], (u / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
-          load(nxt);
+        // refill the stage of the previous tile (its MMAs have had a whole
+        // iteration to finish), not the one just issued
+        if (u >= 1) {
+          const int pv = u - 1;
+          const int nxt = pv + kStages2;
+          if (nxt < my_tiles) {
+            if (!mbar_wait_abort(&s_empty[pv % kStages2], (pv / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
+            load(nxt);
+          }
         }
       }
     }
@@ -456,11 +461,11 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
             const int clj = (j >> 1) / S;
             const int b = (j >> 1) % S;
             if (mine && clj == cl && b >= a) {
-              float2* o = dst + bl_index(a, b, S);
-              float2 x = *o;
-              x.x += m0 + n1;
-              x.y += n0 - m1;
-              *o = x;
+              // each partial-sum element gets exactly one add per launch, so a
+              // fire-and-forget reduction keeps the sums deterministic
+              float* o = reinterpret_cast<float*>(dst + bl_index(a, b, S));
+              atomicAdd(o, m0 + n1);
+              atomicAdd(o + 1, n0 - m1);
             }
           }
         }

@@ -171,11 +171,11 @@ __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
 #pragma unroll
     for (int j = i; j < TA; ++j)
       if (i < S && j < S) {
-        float2* dst = p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) * (size_t)p.nchan + k;
-        float2 v = *dst;
-        v.x += acc[i][j].x;
-        v.y += acc[i][j].y;
-        *dst = v;
+        // one add per element per launch: deterministic fire-and-forget reduction
+        float* dst = reinterpret_cast<float*>(p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) *
+                                                           (size_t)p.nchan + k);
+        atomicAdd(dst, acc[i][j].x);
+        atomicAdd(dst + 1, acc[i][j].y);
       }
 }
 
