@@ -145,6 +145,14 @@ int corr_wait_pushes(corr_t *h);
  * that station afterwards. */
 int corr_attach_samples_device(corr_t *h, int station, const void *dev_bytes, size_t nbytes);
 
+/* Use nbytes of packed samples in pinned (page-locked, mapped) host memory as
+ * the station's whole stream without copying it: the F step's loads read the
+ * samples over the host link (on GB300, NVLink-C2C) as it needs them, each
+ * byte once.  16-byte aligned, nbytes a multiple of 4; the caller keeps the
+ * memory alive and unchanged until corr_destroy or corr_reset.  No push is
+ * allowed for that station afterwards. */
+int corr_attach_samples_host(corr_t *h, int station, const void *host_bytes, size_t nbytes);
+
 /* Declare the end of data: integrations that reach past a station's data are
  * then produced with those blocks marked invalid instead of CORR_EAGAIN. */
 int corr_flush(corr_t *h);

@@ -62,6 +62,7 @@ _SIGS = {
     "corr_push_samples_async": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
     "corr_wait_pushes": ([_H], C.c_int),
     "corr_attach_samples_device": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
+    "corr_attach_samples_host": ([_H, C.c_int, _P, C.c_size_t], C.c_int),
     "corr_flush": ([_H], C.c_int),
     "corr_correlate": ([_H, _P, _P], C.c_int),
     "corr_correlate_device": ([_H, _P, _P], C.c_int),
@@ -196,6 +197,13 @@ class Correlator:
         self._keep.append(dev_tensor)
         n = dev_tensor.numel() * dev_tensor.element_size()
         self._check(corr_attach_samples_device(self.h, station, dev_tensor.data_ptr(), n))
+
+    def attach_host(self, station: int, pinned):
+        """Use a pinned host tensor (or array) as the station's whole stream,
+        read by the kernels over the host link without a copy (kept alive here)."""
+        self._keep.append(pinned)
+        n = pinned.nbytes if isinstance(pinned, np.ndarray) else pinned.numel() * pinned.element_size()
+        self._check(corr_attach_samples_host(self.h, station, _ptr(pinned), n))
 
     def flush(self):
         self._check(corr_flush(self.h))

@@ -833,6 +833,32 @@ int corr_attach_samples_device(corr_t* h, int station, const void* dev_bytes, si
   return CORR_OK;
 }
 
+int corr_attach_samples_host(corr_t* h, int station, const void* host_bytes, size_t nbytes) {
+  if (!h) return CORR_EINVAL;
+  if (station < 0 || station >= h->S) return h->fail(CORR_EINVAL, "corr_attach_samples_host: station out of range");
+  if (nbytes % 4) return h->fail(CORR_EINVAL, "corr_attach_samples_host: nbytes must be a multiple of 4");
+  if (!host_bytes || ((uintptr_t)host_bytes & 15))
+    return h->fail(CORR_EINVAL, "corr_attach_samples_host: pointer must be non-NULL and 16-byte aligned");
+  Station& s = h->st[station];
+  if (s.started) return h->fail(CORR_ESTATE, "corr_attach_samples_host: station already has data");
+  int rc = use_device(h);
+  if (rc) return rc;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, host_bytes);
+  if (e != cudaSuccess || at.type != cudaMemoryTypeHost || !at.devicePointer) {
+    cudaGetLastError();
+    return h->fail(CORR_EINVAL, "corr_attach_samples_host: not pinned (page-locked, mapped) host memory");
+  }
+  cudaFree(s.dbuf);
+  s.dbuf = nullptr;
+  s.cap = 0;
+  s.ext = (const uint8_t*)at.devicePointer;  // the device-side address of the pinned pages
+  s.len = nbytes;
+  s.attached = true;
+  s.started = true;
+  return CORR_OK;
+}
+
 int corr_flush(corr_t* h) {
   if (!h) return CORR_EINVAL;
   h->flushed = true;

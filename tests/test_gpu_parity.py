@@ -309,3 +309,22 @@ def test_async_pushes_in_pieces_match_oracle(corr):
         err = rel_rms_per_baseline(v.reshape(sc.nbl, sc.G, sc.nchan), ref[i])
         assert np.all(err < TOL_FP32), (i, err.max())
     c.close()
+
+
+def test_host_attached_streams_match_oracle(corr):
+    """Stations' packed bytes left in pinned host memory and attached with
+    corr_attach_samples_host (read by the F kernel over the host link)."""
+    import torch
+    sc, streams = small_cfg2(duration=0.06, tint=0.02, nchan=512, stations=5, nsub=4, npol=2)
+    ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 3)
+    pinned = [torch.from_numpy(b).pin_memory() for b in streams]
+    c = corr.from_scan(sc)
+    for s in range(sc.stations):
+        c.attach_host(s, pinned[s])
+    c.flush()
+    vis, w = run_all(c, 3)
+    assert np.array_equal(w, wref)
+    for i in range(3):
+        err = rel_rms_per_baseline(vis[i].reshape(sc.nbl, sc.G, sc.nchan), ref[i])
+        assert np.all(err < TOL_FP32), (i, err.max())
+    c.close()
