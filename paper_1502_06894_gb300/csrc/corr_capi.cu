@@ -447,7 +447,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   CK(cudaMemcpyAsync(h->h_stat, h->d_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyDeviceToHost, h->stream),
      "stat D2H");
   CK(cudaStreamSynchronize(h->stream), "delay_blocks");
-  if (*h->h_err) return h->fail(CORR_ETIMEOUT, "a tensor-core X-step wait timed out on the device");
+  if (*h->h_err) return h->fail(CORR_ETIMEOUT, "an X-step wait timed out on the device");
   const unsigned long long off = 1ull << 62;
   // the compute stream waits for the asynchronous pushes holding the bytes
   // this integration reads (pieces that start below the last byte needed)
@@ -548,6 +548,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
       xp.nchan = h->nchan;
       xp.KZ = h->KZ;
       xp.part = h->d_part;
+      xp.err = h->d_err;
       pa = prof_begin(h);
       CK(launch_xstage(xp, h->stream), "xstage launch");
       prof_end(h, 2, pa);
@@ -574,7 +575,7 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   else
     CK(launch_finalize(fin, h->stream), "finalize launch");
   prof_end(h, 3, pa);
-  if (tc) CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "error flag D2H");
+  CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "error flag D2H");
   h->next_int = i + 1;
   return CORR_OK;
 }
@@ -880,7 +881,7 @@ int corr_correlate(corr_t* h, float* out, double* weights) {
       e = cudaMemcpyAsync(weights, dw, sizeof(double) * nbl_of(h->S), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) rc = h->cuda_fail(e, "correlate D2H");
-    else if (*h->h_err) rc = h->fail(CORR_ETIMEOUT, "a tensor-core X-step wait timed out on the device");
+    else if (*h->h_err) rc = h->fail(CORR_ETIMEOUT, "an X-step wait timed out on the device");
   }
   return rc;
 }

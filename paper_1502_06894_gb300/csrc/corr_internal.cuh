@@ -99,6 +99,7 @@ struct XParams {
   int CB, S, G, nchan;
   int KZ;                   // block splits per chunk (one partial each)
   float2* part;             // [KZ][nbl][G][nchan]
+  int* err;                 // set to 1 when a device wait times out (may be null)
 };
 
 struct FinParams {

@@ -210,6 +210,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     xp.nchan = nchan;
     xp.KZ = KZ;
     xp.part = (float2*)(base + o_part);
+    xp.err = nullptr;
     e = launch_xstage(xp, st);
   }
   if (e == cudaSuccess) {

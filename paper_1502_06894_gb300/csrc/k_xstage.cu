@@ -12,6 +12,10 @@
 // are deterministic and the FP32 sums stay short (hierarchical accumulation).
 #include "corr_internal.cuh"
 
+#include <cuda.h>
+#include <type_traits>
+#include <cudaTypedefs.h>
+
 namespace corr {
 
 constexpr int kXT = 128;  // threads per CTA (channels)
@@ -179,6 +183,199 @@ __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
       }
 }
 
+// The same X step with the ring filled by the tensor memory accelerator: one
+// 2-D tensor copy per stage (box: 128 channels x (kNB blocks x S stations))
+// instead of 16-byte copies from every thread, so the bytes in flight are not
+// limited by per-thread outstanding requests.  Thread 0 issues the copies; an
+// mbarrier with a transaction count per ring slot signals arrival; every wait
+// is bounded (timeout -> *err, the CTA stops issuing and returns).
+// First tile row of part `part` of `npart` for a triangular tile: the parts
+// get about equal numbers of baselines (row i holds TA - i of them).
+__host__ __device__ constexpr int tri_split(int TA, int npart, int part) {
+  if (part <= 0) return 0;
+  if (part >= npart) return TA;
+  int acc = 0, i = 0;
+  const int total = TA * (TA + 1) / 2;
+  while (i < TA && 2 * npart * (acc + (TA - i)) <= 2 * total * part + npart * (TA - i)) {
+    acc += TA - i;
+    ++i;
+  }
+  return i;
+}
+
+constexpr long kXWaitLimit = 1L << 26;
+
+__device__ __forceinline__ uint32_t xs_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
+
+// Two threads per channel (256 per CTA): thread part 0 owns tile rows
+// [0, SPLIT), part 1 rows [SPLIT, TA) -- about half the baselines each --
+// so twice the warps share one ring of spectra.
+constexpr int kXThreadsT = 2 * kXT;
+
+template <int TA>
+__global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__ CUtensorMap tmap, XParams p) {
+  extern __shared__ __align__(1024) unsigned char xs_raw[];
+  const uint32_t raw = xs_u32(xs_raw);
+  float2* ring = reinterpret_cast<float2*>(xs_raw + (((raw + 1023u) & ~1023u) - raw));  // [kStagesX][kNB*S][kXT]
+  __shared__ __align__(8) uint64_t full[kStagesX];
+  __shared__ int s_abort;
+  const int tid = threadIdx.x;
+  const int lane_ch = tid % kXT;
+  const int part = tid / kXT;
+  const int k0 = blockIdx.x * kXT;
+  const int k = k0 + lane_ch;
+  const int g = blockIdx.y;
+  const int kz = blockIdx.z;
+  const int S = p.S;
+  const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
+  const int b_hi = (int)((int64_t)p.CB * (kz + 1) / p.KZ);
+  if (b_hi <= b_lo) return;
+  const int nst = (b_hi - b_lo + kNB - 1) / kNB;
+  const int stage_elems = kNB * S * kXT;
+  const uint32_t stage_bytes = (uint32_t)stage_elems * 8u;
+  if (tid == 0) {
+    for (int i = 0; i < kStagesX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xs_u32(&full[i])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  auto issue = [&](int q) {
+    if (q >= nst) return;
+    const int slot = q % kStagesX;
+    const int row = (g * p.CB + b_lo + q * kNB) * S;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xs_u32(&full[slot])),
+                 "r"(stage_bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            xs_u32(ring + slot * stage_elems)),
+        "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(2 * k0), "r"(row), "r"(xs_u32(&full[slot]))
+        : "memory");
+  };
+
+  float2 acc[TA][TA];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  if (tid == 0)
+    for (int q = 0; q < kStagesX - 1; ++q) issue(q);
+
+  // rows [I0, I1) of this thread's part, compile-time per branch
+  auto run = [&](auto I0c, auto I1c) {
+    constexpr int I0 = decltype(I0c)::value, I1 = decltype(I1c)::value;
+    int q = 0;
+    for (; q < nst; ++q) {
+      if (tid == 0) issue(q + kStagesX - 1);  // the slot of stage q-1, freed by the sync below
+      const int slot = q % kStagesX;
+      uint32_t ok = 0;
+      for (long it = 0; it < kXWaitLimit && !ok; ++it) {
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(xs_u32(&full[slot])), "r"((uint32_t)((q / kStagesX) & 1))
+            : "memory");
+        if ((it & 1023) == 1023 && s_abort) break;
+      }
+      if (!ok) s_abort = 1;
+      __syncthreads();
+      if (s_abort) break;
+      const float2* st = ring + slot * stage_elems;
+#pragma unroll
+      for (int bi = 0; bi < kNB; ++bi) {
+        if (b_lo + q * kNB + bi >= b_hi) break;
+        float2 a[TA];
+#pragma unroll
+        for (int i = I0; i < TA; ++i) a[i] = i < S ? st[(bi * S + i) * kXT + lane_ch] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = I0; i < I1; ++i)
+#pragma unroll
+          for (int j = i; j < TA; ++j) {
+            acc[i][j].x = fmaf(a[i].x, a[j].x, fmaf(a[i].y, a[j].y, acc[i][j].x));
+            acc[i][j].y = fmaf(a[i].y, a[j].x, fmaf(-a[i].x, a[j].y, acc[i][j].y));
+          }
+      }
+      __syncthreads();
+    }
+    if (s_abort) {
+      // let the copies already issued land before the CTA's shared memory goes away
+      if (tid == 0) {
+        for (int r = q + 1; r < q + kStagesX && r < nst; ++r) {
+          const int slot = r % kStagesX;
+          uint32_t ok = 0;
+          for (long it = 0; it < kXWaitLimit && !ok; ++it)
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                : "=r"(ok)
+                : "r"(xs_u32(&full[slot])), "r"((uint32_t)((r / kStagesX) & 1))
+                : "memory");
+        }
+        if (p.err) atomicExch(p.err, 1);
+      }
+      return;
+    }
+    if (k >= p.nchan) return;
+    const int nbl = nbl_of(S);
+#pragma unroll
+    for (int i = I0; i < I1; ++i)
+#pragma unroll
+      for (int j = i; j < TA; ++j)
+        if (i < S && j < S) {
+          float* dst = reinterpret_cast<float*>(p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) *
+                                                             (size_t)p.nchan + k);
+          atomicAdd(dst, acc[i][j].x);
+          atomicAdd(dst + 1, acc[i][j].y);
+        }
+  };
+  constexpr int SPLIT = tri_split(TA, 2, 1);
+  if (part == 0)
+    run(std::integral_constant<int, 0>{}, std::integral_constant<int, SPLIT>{});
+  else
+    run(std::integral_constant<int, SPLIT>{}, std::integral_constant<int, TA>{});
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+template <int TA>
+static cudaError_t launch_tma(const XParams& p, cudaStream_t s, bool* used) {
+  *used = false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || p.nchan < kXT || kNB * p.S > 256) return cudaSuccess;
+  CUtensorMap tm;
+  cuuint64_t dims[2] = {(cuuint64_t)2 * p.nchan, (cuuint64_t)p.G * p.CB * p.S};
+  cuuint64_t strides[1] = {(cuuint64_t)2 * p.nchan * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * kXT), (cuuint32_t)(kNB * p.S)};
+  cuuint32_t estr[2] = {1, 1};
+  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(p.spec), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaSuccess;  // fall back to the cp.async ring
+  const size_t smem = 1024 + (size_t)kStagesX * kNB * p.S * kXT * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_xmac_tma<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((p.nchan + kXT - 1) / kXT, p.G, p.KZ);
+  k_xmac_tma<TA><<<grid, kXThreadsT, smem, s>>>(tm, p);
+  *used = true;
+  return cudaGetLastError();
+}
+
 static int tile_for(int S) {
   if (S <= 2) return 2;
   if (S <= 4) return 4;
@@ -204,6 +401,9 @@ int xstage_kz(int CB, int S, int G, int nchan) {
 
 template <int TA>
 static cudaError_t launch_ring(const XParams& p, cudaStream_t s) {
+  bool used = false;
+  cudaError_t te = launch_tma<TA>(p, s, &used);
+  if (te != cudaSuccess || used) return te;
   const size_t smem = (size_t)kStagesX * kNB * p.S * kXT * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_xmac_ring<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
