@@ -186,6 +186,28 @@ const char *corr_last_error(const corr_t *h);
 /* Free the handle and its device memory (NULL is allowed). */
 void corr_destroy(corr_t *h);
 
+/* ---- several scans at once ------------------------------------------------
+ *
+ * Correlate the next integration of each of n handles in one launch: their
+ * device work is recorded as parallel branches of one CUDA graph (up to 16
+ * concurrent branches) and the graph is launched on cuda_stream (NULL: an
+ * internal stream).  dev_out[j] / dev_weights[j] (device memory, weights may
+ * be NULL) receive handle j's visibilities in the corr_correlate_device
+ * layout.  Every handle must live on the current device, have corr_flush
+ * called (its samples all pushed or attached) and profiling off; blocks
+ * without data simply get zero weight.  Returns once the graph is launched;
+ * synchronise cuda_stream before reading the outputs.  Each handle's
+ * integration counter advances by one.  Not thread-safe per device. */
+int corr_batch_run(corr_t *const *handles, int n, float *const *dev_out, double *const *dev_weights,
+                   void *cuda_stream);
+
+/* Device memory the handle holds once prepared: work buffers sized by the
+ * shape, precision and chunk setting, plus sample buffers it owns (attached
+ * samples are not counted).  Available before the first correlate, for
+ * admission control by a scheduler.  CORR_EINVAL if fs*tint is not a whole
+ * number of samples >= 2*nchan. */
+int corr_device_bytes(corr_t *h, size_t *bytes);
+
 /* ---- inspection of intermediate results (for tests; slow) ---------------- */
 
 /* Delay-block results for blocks [b0, b0+nb) of all stations, each array

@@ -78,6 +78,8 @@ _SIGS = {
     "corr_read_profile": ([_H, _P, _P], C.c_int),
     "corr_launch_shape": ([_H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "corr_correlate_static": ([C.POINTER(CorrScanDesc), C.c_int64, _P, _P, _P], C.c_int),
+    "corr_batch_run": ([_P, C.c_int, _P, _P, _P], C.c_int),
+    "corr_device_bytes": ([_H, C.POINTER(C.c_size_t)], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -237,6 +239,11 @@ class Correlator:
             self._check(rc)
         return rc
 
+    def device_bytes(self) -> int:
+        v = C.c_size_t()
+        self._check(corr_device_bytes(self.h, C.byref(v)))
+        return v.value
+
     def next_integration(self) -> int:
         v = C.c_int64()
         self._check(corr_next_integration(self.h, C.byref(v)))
@@ -329,4 +336,17 @@ class StaticScan:
     def correlate(self, integration: int, dev_out, dev_weights=None, stream: Optional[int] = None) -> int:
         return corr_correlate_static(C.byref(self.desc), int(integration), _ptr(dev_out), _ptr(dev_weights),
                                      stream)
+
+
+def batch_run(correlators, dev_outs, dev_weights=None, stream=None) -> int:
+    """Next integration of every Correlator as one CUDA graph (corr_batch_run)."""
+    n = len(correlators)
+    hs = (C.c_void_p * n)(*[c.h.value for c in correlators])
+    outs = (C.c_void_p * n)(*[_ptr(o) for o in dev_outs])
+    ws = (C.c_void_p * n)(*[_ptr(w) for w in dev_weights]) if dev_weights is not None else None
+    rc = corr_batch_run(C.cast(hs, C.c_void_p), n, C.cast(outs, C.c_void_p),
+                        C.cast(ws, C.c_void_p) if ws is not None else None, stream)
+    if rc != CORR_OK:
+        raise CorrError(rc, "corr_batch_run failed: " + corr_last_error(correlators[0].h).decode())
+    return rc
 

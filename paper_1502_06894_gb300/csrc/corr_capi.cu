@@ -76,6 +76,7 @@ struct corr_s {
   // device state
   StationView* d_views = nullptr;
   StationView* h_views = nullptr;  // pinned staging
+  bool views_valid = false;        // h_views holds the device copy
   int* d_nseg = nullptr;
   double* d_seg_t0 = nullptr;
   double* d_seg_c = nullptr;
@@ -246,6 +247,7 @@ static void free_device(corr_t* h) {
   h->d_twN = nullptr; h->d_spec = nullptr; h->d_part = nullptr; h->d_out = nullptr;
   h->d_wcount = nullptr;
   h->prepared = false;
+  h->views_valid = false;
 }
 
 static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
@@ -257,14 +259,54 @@ static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
   return CORR_OK;
 }
 
+// Sizes of the work buffers, from the handle's shape alone (shared by the
+// allocation and by the memory estimate a scheduler asks for).
+struct WorkLayout {
+  int64_t spi = 0;
+  int Mcap = 0, CB = 0, KZ = 0, KZ_tc = 0, kz_alloc = 0;
+  bool tiles = false;
+  size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;
+  size_t total() const { return spec + part + tiles_bytes + small; }
+};
+
+static int work_layout(corr_t* h, WorkLayout& w) {
+  const double spi = h->fs * h->tint;
+  if (fabs(spi - (double)llround(spi)) > 1e-6 || llround(spi) < h->N)
+    return h->fail(CORR_EINVAL, "fs*tint = %.9g must be a whole number of samples >= 2*nchan", spi);
+  w.spi = llround(spi);
+  const int S = h->S, G = h->G, nch = h->nchan;
+  const size_t nbl = (size_t)nbl_of(S);
+  w.Mcap = (int)((w.spi + h->N - 1) / h->N) + 1;
+  const size_t per_block = (size_t)G * S * nch * sizeof(float2);
+  int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
+  if (cb < 1) cb = 1;
+  if (cb > w.Mcap) cb = w.Mcap;
+  w.CB = (int)cb;
+  w.KZ = xstage_kz(w.CB, S, G, nch);
+  w.KZ_tc = (w.CB + kTcBlocks - 1) / kTcBlocks;
+  w.kz_alloc = w.KZ > w.KZ_tc ? w.KZ : w.KZ_tc;
+  w.tiles = h->precision == CORR_PREC_FP16_TC && fstage_tc_tiles_supported(nch);
+  // in tile mode the F step writes the operand tiles, not a spectra buffer
+  w.spec = w.tiles ? 16 : per_block * w.CB;
+  w.part = sizeof(float2) * (size_t)w.kz_alloc * nbl * G * nch;
+  if (w.tiles) {
+    const int W = 2 * xtc_cpt(S);
+    w.tiles_bytes = (size_t)G * ((nch + W - 1) / W) * ((size_t)(w.CB + 63) / 64) * 32768;
+  }
+  const size_t M = (size_t)w.Mcap;
+  w.small = sizeof(StationView) * S + sizeof(int) * S + sizeof(double) * S * kMaxSegs * 7 +
+            sizeof(double) * h->nsub + (sizeof(int64_t) + sizeof(float) + 1) * S * M +
+            sizeof(float) * S * h->nsub * M + sizeof(unsigned long long) * 3 * S + sizeof(float2) * h->N +
+            sizeof(float2) * nbl * G * nch + (sizeof(int) + sizeof(double)) * nbl + sizeof(int);
+  return CORR_OK;
+}
+
 static int prepare(corr_t* h) {
   if (h->prepared) return CORR_OK;
-  {
-    const double spi = h->fs * h->tint;
-    if (fabs(spi - (double)llround(spi)) > 1e-6 || llround(spi) < h->N)
-      return h->fail(CORR_EINVAL, "fs*tint = %.9g must be a whole number of samples >= 2*nchan", spi);
-    h->spi = llround(spi);
-  }
+  WorkLayout w;
+  int rc;
+  if ((rc = work_layout(h, w))) return rc;
+  h->spi = w.spi;
   {
     std::lock_guard<std::mutex> lk(g_const_mu);
     if (h->dev >= 0 && h->dev < 64 && !g_const_ready[h->dev]) {
@@ -273,22 +315,16 @@ static int prepare(corr_t* h) {
     }
   }
   const int S = h->S, G = h->G, nch = h->nchan, nbl = nbl_of(S);
-  h->Mcap = (int)((h->spi + h->N - 1) / h->N) + 1;
-  const size_t per_block = (size_t)G * S * nch * sizeof(float2);
-  int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
-  if (cb < 1) cb = 1;
-  if (cb > h->Mcap) cb = h->Mcap;
-  h->CB = (int)cb;
-  h->KZ = xstage_kz(h->CB, S, G, nch);
-  h->KZ_tc = (h->CB + kTcBlocks - 1) / kTcBlocks;
+  h->Mcap = w.Mcap;
+  h->CB = w.CB;
+  h->KZ = w.KZ;
+  h->KZ_tc = w.KZ_tc;
   {
     int lg = 0;
     while ((1 << (lg + 1)) <= h->N) ++lg;
     h->sigma = lg / 2;
   }
   CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev), "SM count");
-  const int kz_alloc = h->KZ > h->KZ_tc ? h->KZ : h->KZ_tc;
-  int rc;
   if ((rc = dalloc(h, (void**)&h->d_views, sizeof(StationView) * S, "views"))) return rc;
   CK(cudaMallocHost((void**)&h->h_views, sizeof(StationView) * S), "cudaMallocHost views");
   if ((rc = dalloc(h, (void**)&h->d_nseg, sizeof(int) * S, "nseg"))) return rc;
@@ -302,22 +338,18 @@ static int prepare(corr_t* h) {
   if ((rc = dalloc(h, (void**)&h->d_stat, sizeof(unsigned long long) * 3 * S, "stat"))) return rc;
   CK(cudaMallocHost((void**)&h->h_stat, sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
   if ((rc = dalloc(h, (void**)&h->d_twN, sizeof(float2) * h->N, "twiddles"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_spec, per_block * h->CB, "spectra"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_part, sizeof(float2) * (size_t)kz_alloc * nbl * G * nch, "partials"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_spec, w.spec, "spectra"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_part, w.part, "partials"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_out, sizeof(float2) * (size_t)nbl * G * nch, "out"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wcount, sizeof(int) * nbl, "wcount"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wts, sizeof(double) * nbl, "weights"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_err, sizeof(int), "error flag"))) return rc;
   CK(cudaMallocHost((void**)&h->h_err, sizeof(int)), "cudaMallocHost err");
-  h->tc_tiles = h->precision == CORR_PREC_FP16_TC && fstage_tc_tiles_supported(nch);
+  h->tc_tiles = w.tiles;
   if (h->tc_tiles) {
-    const int W = 2 * xtc_cpt(S);
-    const size_t nslice = (size_t)(nch + W - 1) / W;
-    const size_t nkt = (size_t)(h->CB + 63) / 64;
-    const size_t bytes = (size_t)G * nslice * nkt * 32768;
-    if ((rc = dalloc(h, (void**)&h->d_tiles, bytes, "operand tiles"))) return rc;
+    if ((rc = dalloc(h, (void**)&h->d_tiles, w.tiles_bytes, "operand tiles"))) return rc;
     // rows beyond the stations of a tile stay zero for good
-    CK(cudaMemset(h->d_tiles, 0, bytes), "operand tiles clear");
+    CK(cudaMemset(h->d_tiles, 0, w.tiles_bytes), "operand tiles clear");
   }
   *h->h_err = 0;
   CK(cudaMemset(h->d_err, 0, sizeof(int)), "error flag reset");
@@ -353,19 +385,24 @@ static int upload_model(corr_t* h) {
     CK(cudaMemcpy(h->d_nu0, h->nu0.data(), sizeof(double) * h->nsub, cudaMemcpyHostToDevice), "nu0 H2D");
     h->polys_dirty = false;
   }
-  // station views: small pinned staging copied on the stream
-  CK(cudaStreamSynchronize(h->stream), "sync before view update");
+  // station views: the pinned staging copy holds what the device has; copy
+  // again only when a push or attach changed them
+  std::vector<StationView> views(S);
   for (int s = 0; s < S; ++s) {
     const Station& x = h->st[s];
-    StationView v;
+    StationView& v = views[s];
+    memset(&v, 0, sizeof(v));
     v.words = reinterpret_cast<const uint32_t*>(station_ptr(x));
     v.nwords = (int64_t)(x.len / 4);
     v.sample0 = x.sample0;
     v.ngroups = station_groups(h, x);
-    h->h_views[s] = v;
   }
+  if (h->views_valid && memcmp(views.data(), h->h_views, sizeof(StationView) * S) == 0) return CORR_OK;
+  CK(cudaStreamSynchronize(h->stream), "sync before view update");
+  memcpy(h->h_views, views.data(), sizeof(StationView) * S);
   CK(cudaMemcpyAsync(h->d_views, h->h_views, sizeof(StationView) * S, cudaMemcpyHostToDevice, h->stream),
      "views H2D");
+  h->views_valid = true;
   return CORR_OK;
 }
 
@@ -417,6 +454,112 @@ static FParams fparams(corr_t* h, int blk0, int cb) {
   p.scale = 1.0f;
   p.out = h->d_spec;
   return p;
+}
+
+// Device work of one integration after its delay blocks are in the
+// descriptor arrays: partial-sum clear, F and X per chunk, weights and
+// normalisation, all on stream st, with no host wait (so it can be recorded
+// into a CUDA graph).  M = blocks of the integration.
+static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, double* w_out) {
+  const int S = h->S;
+  cudaEvent_t pa = nullptr;
+  // F and X per chunk
+  const int nbl = nbl_of(S);
+  const int kz_used = h->precision == CORR_PREC_FP16_TC ? (h->tc_tiles ? 1 : h->KZ_tc) : h->KZ;
+  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, st),
+     "partials memset");
+  const bool tc = h->precision == CORR_PREC_FP16_TC;
+  for (int c0 = 0; c0 < M; c0 += h->CB) {
+    const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
+    FParams fp = fparams(h, c0, cb);
+    if (tc) {
+      fp.out_kind = 1;
+      fp.scale = ldexpf(1.0f, -h->sigma);
+    }
+    if (h->tc_tiles) {
+      // F writes MMA operand tiles; X fetches them with bulk copies
+      TcTiles o;
+      o.tiles = h->d_tiles;
+      o.cpt = xtc_cpt(S);
+      o.W = 2 * o.cpt;
+      o.nslice = (h->nchan + o.W - 1) / o.W;
+      o.NKT = (cb + 63) / 64;
+      o.scale = ldexpf(1.0f, -h->sigma);
+      pa = prof_begin(h);
+      CK(launch_fstage_tc(fp, o, st), "tensor-core fstage launch");
+      prof_end(h, 1, pa);
+      XTC2Params xp;
+      xp.tiles = h->d_tiles;
+      xp.nslice = o.nslice;
+      xp.NKT = o.NKT;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.cpt = o.cpt;
+      xp.W = o.W;
+      xp.part = h->d_part;
+      xp.err = h->d_err;
+      pa = prof_begin(h);
+      CK(launch_xtc2(xp, h->sm_count, st), "tensor-core xstage launch");
+      prof_end(h, 2, pa);
+      continue;
+    }
+    pa = prof_begin(h);
+    CK(launch_fstage(fp, st), "fstage launch");
+    prof_end(h, 1, pa);
+    if (tc) {
+      XTCParams xp;
+      xp.spec = reinterpret_cast<const __half2*>(h->d_spec);
+      xp.CB = cb;
+      xp.cb = cb;
+      xp.kblocks = kTcBlocks;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.cpt = xtc_cpt(S);
+      xp.W = 2 * xp.cpt;
+      xp.part = h->d_part;
+      xp.err = h->d_err;
+      pa = prof_begin(h);
+      CK(launch_xtc(xp, h->sm_count, st), "tensor-core xstage launch");
+      prof_end(h, 2, pa);
+    } else {
+      XParams xp;
+      xp.spec = h->d_spec;
+      xp.CB = cb;
+      xp.S = S;
+      xp.G = h->G;
+      xp.nchan = h->nchan;
+      xp.KZ = h->KZ;
+      xp.part = h->d_part;
+      xp.err = h->d_err;
+      pa = prof_begin(h);
+      CK(launch_xstage(xp, st), "xstage launch");
+      prof_end(h, 2, pa);
+    }
+  }
+  // weights + normalisation
+  FinParams fin;
+  fin.part = h->d_part;
+  fin.KZ = kz_used;
+  fin.S = S;
+  fin.G = h->G;
+  fin.nchan = h->nchan;
+  fin.N = h->N;
+  fin.valid = h->d_valid;
+  fin.ld = h->Mcap;
+  fin.M = M;
+  fin.wcount = h->d_wcount;
+  fin.out = vis_out;
+  fin.weights = w_out;
+  pa = prof_begin(h);
+  CK(launch_weights(fin, st), "weights launch");
+  if (tc)
+    CK(launch_finalize_tc(fin, ldexpf(1.0f, 2 * h->sigma), st), "finalize launch");
+  else
+    CK(launch_finalize(fin, st), "finalize launch");
+  prof_end(h, 3, pa);
+  return CORR_OK;
 }
 
 // The whole schedule of one integration.  On success the visibilities are in
@@ -479,102 +622,8 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   }
   if (h->flushed && !any_data) return h->fail(CORR_EEND, "no station has data for integration %lld", (long long)i);
 
-  // 2. F and X per chunk
-  const int nbl = nbl_of(S);
-  const int kz_used = h->precision == CORR_PREC_FP16_TC ? (h->tc_tiles ? 1 : h->KZ_tc) : h->KZ;
-  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, h->stream),
-     "partials memset");
-  const bool tc = h->precision == CORR_PREC_FP16_TC;
-  for (int c0 = 0; c0 < M; c0 += h->CB) {
-    const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
-    FParams fp = fparams(h, c0, cb);
-    if (tc) {
-      fp.out_kind = 1;
-      fp.scale = ldexpf(1.0f, -h->sigma);
-    }
-    if (h->tc_tiles) {
-      // F writes MMA operand tiles; X fetches them with bulk copies
-      TcTiles o;
-      o.tiles = h->d_tiles;
-      o.cpt = xtc_cpt(S);
-      o.W = 2 * o.cpt;
-      o.nslice = (h->nchan + o.W - 1) / o.W;
-      o.NKT = (cb + 63) / 64;
-      o.scale = ldexpf(1.0f, -h->sigma);
-      pa = prof_begin(h);
-      CK(launch_fstage_tc(fp, o, h->stream), "tensor-core fstage launch");
-      prof_end(h, 1, pa);
-      XTC2Params xp;
-      xp.tiles = h->d_tiles;
-      xp.nslice = o.nslice;
-      xp.NKT = o.NKT;
-      xp.S = S;
-      xp.G = h->G;
-      xp.nchan = h->nchan;
-      xp.cpt = o.cpt;
-      xp.W = o.W;
-      xp.part = h->d_part;
-      xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xtc2(xp, h->sm_count, h->stream), "tensor-core xstage launch");
-      prof_end(h, 2, pa);
-      continue;
-    }
-    pa = prof_begin(h);
-    CK(launch_fstage(fp, h->stream), "fstage launch");
-    prof_end(h, 1, pa);
-    if (tc) {
-      XTCParams xp;
-      xp.spec = reinterpret_cast<const __half2*>(h->d_spec);
-      xp.CB = cb;
-      xp.cb = cb;
-      xp.kblocks = kTcBlocks;
-      xp.S = S;
-      xp.G = h->G;
-      xp.nchan = h->nchan;
-      xp.cpt = xtc_cpt(S);
-      xp.W = 2 * xp.cpt;
-      xp.part = h->d_part;
-      xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xtc(xp, h->sm_count, h->stream), "tensor-core xstage launch");
-      prof_end(h, 2, pa);
-    } else {
-      XParams xp;
-      xp.spec = h->d_spec;
-      xp.CB = cb;
-      xp.S = S;
-      xp.G = h->G;
-      xp.nchan = h->nchan;
-      xp.KZ = h->KZ;
-      xp.part = h->d_part;
-      xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xstage(xp, h->stream), "xstage launch");
-      prof_end(h, 2, pa);
-    }
-  }
-  // 3. weights + normalisation
-  FinParams fin;
-  fin.part = h->d_part;
-  fin.KZ = kz_used;
-  fin.S = S;
-  fin.G = h->G;
-  fin.nchan = h->nchan;
-  fin.N = h->N;
-  fin.valid = h->d_valid;
-  fin.ld = h->Mcap;
-  fin.M = M;
-  fin.wcount = h->d_wcount;
-  fin.out = vis_out;
-  fin.weights = w_out;
-  pa = prof_begin(h);
-  CK(launch_weights(fin, h->stream), "weights launch");
-  if (tc)
-    CK(launch_finalize_tc(fin, ldexpf(1.0f, 2 * h->sigma), h->stream), "finalize launch");
-  else
-    CK(launch_finalize(fin, h->stream), "finalize launch");
-  prof_end(h, 3, pa);
+  int rc2 = enqueue_rest(h, h->stream, M, vis_out, w_out);
+  if (rc2) return rc2;
   CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "error flag D2H");
   h->next_int = i + 1;
   return CORR_OK;
@@ -956,6 +1005,130 @@ void corr_destroy(corr_t* h) {
   delete h;
 }
 
+// ---- several handles in one CUDA graph -----------------------------------------
+
+namespace {
+constexpr int kBatchStreams = 16;
+// per-device streams, events and the last instantiated graph of corr_batch_run
+struct BatchCtx {
+  bool ready = false;
+  cudaStream_t st[kBatchStreams] = {};
+  cudaEvent_t fork = nullptr, done = nullptr, join[kBatchStreams] = {};
+  cudaGraphExec_t exec = nullptr;
+};
+BatchCtx g_batch[64];
+std::mutex g_batch_mu;
+}  // namespace
+
+int corr_batch_run(corr_t* const* hs, int n, float* const* dev_out, double* const* dev_weights, void* cuda_stream) {
+  if (!hs || n < 1 || !dev_out) return CORR_EINVAL;
+  for (int j = 0; j < n; ++j)
+    if (!hs[j] || !dev_out[j]) return CORR_EINVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return CORR_ECUDA;
+  for (int j = 0; j < n; ++j) {
+    corr_t* h = hs[j];
+    for (int k = 0; k < j; ++k)
+      if (hs[k] == h) return h->fail(CORR_EINVAL, "corr_batch_run: a handle appears twice");
+    if (h->dev != dev) return h->fail(CORR_EINVAL, "corr_batch_run: handles must live on the current device");
+    if (!h->flushed) return h->fail(CORR_ESTATE, "corr_batch_run: call corr_flush on every handle first");
+    if (h->profiling) return h->fail(CORR_ESTATE, "corr_batch_run: profiling must be off");
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchCtx& b = g_batch[dev];
+  cudaError_t e = cudaSuccess;
+  if (!b.ready) {
+    for (int q = 0; q < kBatchStreams && e == cudaSuccess; ++q)
+      e = cudaStreamCreateWithFlags(&b.st[q], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+    for (int q = 0; q < kBatchStreams && e == cudaSuccess; ++q)
+      e = cudaEventCreateWithFlags(&b.join[q], cudaEventDisableTiming);
+    if (e != cudaSuccess) return hs[0]->cuda_fail(e, "corr_batch_run: streams");
+    b.ready = true;
+  }
+  // everything that waits on the host or allocates happens before the capture
+  for (int j = 0; j < n; ++j) {
+    corr_t* h = hs[j];
+    int rc;
+    if ((rc = prepare(h)) || (rc = upload_model(h)) || (rc = drain_pushes(h))) return rc;
+    for (Station& x : h->st) {
+      for (auto& pe : x.pending) cudaEventDestroy(pe.ev);
+      x.pending.clear();
+    }
+    CK(cudaStreamSynchronize(h->stream), "corr_batch_run: handle stream");
+    if (*h->h_err) return h->fail(CORR_ETIMEOUT, "an X-step wait timed out on the device");
+  }
+  cudaStream_t root = cuda_stream ? (cudaStream_t)cuda_stream : b.st[0];
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return hs[0]->cuda_fail(e, "corr_batch_run: begin capture");
+  int rc = CORR_OK, bad = 0;
+  // fork: every branch stream joins the capture behind the root
+  e = cudaEventRecord(b.fork, root);
+  for (int q = 0; q < kBatchStreams && e == cudaSuccess; ++q)
+    if (b.st[q] != root) e = cudaStreamWaitEvent(b.st[q], b.fork, 0);
+  for (int j = 0; j < n && e == cudaSuccess && rc == CORR_OK; ++j) {
+    corr_t* h = hs[j];
+    cudaStream_t st = b.st[j % kBatchStreams];
+    const int64_t i = h->next_int;
+    const int64_t bfirst = integ_first_block(h, i);
+    const int M = (int)(integ_first_block(h, i + 1) - bfirst);
+    bad = j;
+    e = launch_delay_blocks(delay_params(h, bfirst, M, h->Mcap), st);
+    if (e != cudaSuccess) break;
+    rc = enqueue_rest(h, st, M, reinterpret_cast<float2*>(dev_out[j]), dev_weights ? dev_weights[j] : nullptr);
+    if (rc == CORR_OK) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  }
+  // join every branch back into the root
+  for (int q = 0; q < kBatchStreams && e == cudaSuccess; ++q) {
+    if (b.st[q] == root) continue;
+    e = cudaEventRecord(b.join[q], b.st[q]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(root, b.join[q], 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (rc != CORR_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return rc != CORR_OK ? rc : hs[bad]->cuda_fail(e, "corr_batch_run: capture");
+  }
+  // reuse the executable graph when only parameters changed
+  if (b.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(b.exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(b.exec);
+      b.exec = nullptr;
+    }
+  }
+  if (!b.exec) e = cudaGraphInstantiate(&b.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e == cudaSuccess) e = cudaGraphLaunch(b.exec, root);
+  if (e == cudaSuccess) e = cudaEventRecord(b.done, root);
+  // later work on each handle's own stream comes after the graph
+  for (int j = 0; j < n && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(hs[j]->stream, b.done, 0);
+  if (e != cudaSuccess) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
+    return hs[0]->cuda_fail(e, "corr_batch_run: graph launch");
+  }
+  for (int j = 0; j < n; ++j) hs[j]->next_int += 1;
+  return CORR_OK;
+}
+
+int corr_device_bytes(corr_t* h, size_t* bytes) {
+  if (!h || !bytes) return CORR_EINVAL;
+  WorkLayout w;
+  int rc = work_layout(h, w);
+  if (rc) return rc;
+  size_t total = w.total();
+  for (const Station& x : h->st)
+    if (!x.attached) total += x.cap;  // sample buffers the handle owns
+  *bytes = total;
+  return CORR_OK;
+}
+
 // ---- inspection ------------------------------------------------------------
 
 int corr_set_profiling(corr_t* h, int enable) {
@@ -1046,13 +1219,22 @@ int corr_debug_spectrum(corr_t* h, int station, int stream, int64_t block, float
   // one-block pass through the same kernels, in the handle's work buffers
   DelayParams dp = delay_params(h, block, 1, h->Mcap);
   CK(launch_delay_blocks(dp, h->stream), "delay_blocks");
+  // a buffer of its own: in tensor-core tile mode the handle has no FP32
+  // spectra buffer
+  float2* spec = nullptr;
+  if ((rc = dalloc(h, (void**)&spec, sizeof(float2) * (size_t)h->G * h->S * h->nchan, "debug spectrum"))) return rc;
   FParams fp = fparams(h, 0, 1);
-  CK(launch_fstage(fp, h->stream), "fstage");
-  const float2* src = h->d_spec + ((size_t)stream * 1 * h->S + station) * h->nchan;
-  CK(cudaMemcpyAsync(out, src, sizeof(float2) * h->nchan, cudaMemcpyDeviceToHost, h->stream), "spectrum D2H");
+  fp.out = spec;
+  cudaError_t e = launch_fstage(fp, h->stream);
+  const float2* src = spec + ((size_t)stream * 1 * h->S + station) * h->nchan;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, src, sizeof(float2) * h->nchan, cudaMemcpyDeviceToHost, h->stream);
   uint8_t v = 0;
-  CK(cudaMemcpyAsync(&v, h->d_valid + (size_t)station * h->Mcap, 1, cudaMemcpyDeviceToHost, h->stream), "valid");
-  CK(cudaStreamSynchronize(h->stream), "corr_debug_spectrum");
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&v, h->d_valid + (size_t)station * h->Mcap, 1, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(spec);
+  if (e != cudaSuccess) return h->cuda_fail(e, "corr_debug_spectrum");
   if (valid) *valid = v;
   return CORR_OK;
 }

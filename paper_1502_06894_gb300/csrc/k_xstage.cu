@@ -214,9 +214,9 @@ constexpr int kXThreadsT = 2 * kXT;
 
 template <int TA>
 __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__ CUtensorMap tmap, XParams p) {
-  extern __shared__ __align__(1024) unsigned char xs_raw[];
-  const uint32_t raw = xs_u32(xs_raw);
-  float2* ring = reinterpret_cast<float2*>(xs_raw + (((raw + 1023u) & ~1023u) - raw));  // [kStagesX][kNB*S][kXT]
+  extern __shared__ __align__(1024) unsigned char xs_tma_raw[];
+  const uint32_t raw = xs_u32(xs_tma_raw);
+  float2* ring = reinterpret_cast<float2*>(xs_tma_raw + (((raw + 1023u) & ~1023u) - raw));  // [kStagesX][kNB*S][kXT]
   __shared__ __align__(8) uint64_t full[kStagesX];
   __shared__ int s_abort;
   const int tid = threadIdx.x;

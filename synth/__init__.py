@@ -364,3 +364,42 @@ def config2(seed: int = 2, duration: float = 10.0, tint: float = 1.0, boundary: 
     if plan:
         plan_windows(scan)
     return scan
+
+
+TAG_MIX = 0x4D
+
+
+def scan_mix(seed: int = 4, count: int = 96, fs: float = 32e6, tint_max: float = 1.0,
+             stations=(2, 20), nsub=(1, 16), npol=(1, 2), log2_nchan=(7, 13),
+             duration=(0.5, 30.0)) -> List[Scan]:
+    """A seeded mix of uneven scans: per scan, uniform integers for the
+    station count, subbands and polarisations, a power-of-two channel count
+    drawn uniformly over its exponents, and a duration drawn uniformly in
+    seconds.  Station 0 of every scan is in space; delay polynomials follow
+    the ten-station generator, keyed by the scan's own seed.
+
+    Integrations: the duration is split into ceil(duration / tint_max)
+    integrations of a whole number of FFT blocks each, and the duration is
+    rounded to that, so that every integration is full and at most tint_max
+    long."""
+    r = _rng(seed, TAG_MIX, 0, 0)
+    out = []
+    for q in range(count):
+        S = int(r.integers(stations[0], stations[1] + 1))
+        sb = int(r.integers(nsub[0], nsub[1] + 1))
+        pol = int(r.integers(npol[0], npol[1] + 1))
+        nchan = 1 << int(r.integers(log2_nchan[0], log2_nchan[1] + 1))
+        d = float(r.uniform(duration[0], duration[1]))
+        N = 2 * nchan
+        nint = max(1, math.ceil(d / tint_max - 1e-9))
+        blocks = max(1, int(round(d * fs / nint / N)))
+        tint = blocks * N / fs
+        sc = config2(seed=(seed << 16) + q, duration=nint * tint, tint=tint, boundary=nint * tint / 2,
+                     nchan=nchan, stations=S, nsub=sb, npol=pol, fs=fs)
+        out.append(sc)
+    return out
+
+
+def integrations(scan: Scan) -> int:
+    """Whole integrations in the scan."""
+    return int(round(scan.duration / scan.tint))
