@@ -129,7 +129,9 @@ def test_served_mix_equals_alone(env):
         st = sch.run(jobs)
         return res, st
 
-    mixed, st = run([serve.Job(q, sc, arrival=0.002 * q, precision=1) for q, sc in enumerate(mix)], None)
+    # two jobs at once, the rest arriving while those run
+    arrive = [0.0, 0.0] + [0.0005 * q for q in range(1, len(mix) - 1)]
+    mixed, st = run([serve.Job(q, sc, arrival=arrive[q], precision=1) for q, sc in enumerate(mix)], None)
     assert st["jobs"] == len(mix) and st["max_batch"] >= 2
     assert st["p50_s"] is not None and st["p99_s"] >= st["p50_s"]
     for q, sc in enumerate(mix):
