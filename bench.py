@@ -62,6 +62,14 @@ def parse():
     ap.add_argument("--chunk-blocks", type=int, default=0, help="FFT blocks per F/X chunk (0: library default)")
     ap.add_argument("--duration", type=float, default=10.0,
                     help="scan length in seconds (10 s is the benchmark; shorter only for profiling)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 96-scan batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served leg")
+    ap.add_argument("--batch-scans", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=40.0, help="Poisson arrival rate, jobs/s")
+    ap.add_argument("--serve-window", type=float, default=2.0,
+                    help="seconds of arrivals (the served workload names 120 s; the default is shortened)")
+    ap.add_argument("--hbm-cap", type=float, default=180e9)
+    ap.add_argument("--hbm-reserve", type=float, default=30e9)
     return ap.parse_args()
 
 
@@ -231,6 +239,90 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_leg(args, torch, corr, dev):
+    """96 uneven scans (2-20 stations, 1-16 subbands, 1-2 pols, 128-8192
+    channels, 0.5-30 s): all admitted at once and advanced one integration per
+    step, every step one CUDA graph over all open scans, chunk lengths from
+    the autotuner, FP16 tensor-core X step.  Compared with the same scans one
+    after another through corr_correlate_device (same precision and chunks),
+    and with plain FP32 one after another at the library's default chunks.
+    Samples come from a device-resident pool that every station reads at its
+    own offset."""
+    import synth
+    from paper_1502_06894_gb300 import serve
+    mix = synth.scan_mix(seed=4, count=args.batch_scans)
+    need = max(max(sc.nsamp) * sc.G // 4 for sc in mix)
+    pool = serve.ReplayPool(need + (64 << 20), dev, seed=4)
+    limit = args.hbm_cap - args.hbm_reserve - pool.nbytes
+    tuner = serve.Autotuner(corr, pool, dev, mem_cap=int(limit / len(mix)))
+    TC = corr.CORR_PREC_FP16_TC
+    t0 = time.perf_counter()
+    for sc in mix:
+        tuner.choose(sc, TC)
+    tune_s = time.perf_counter() - t0
+    samples = sum(sc.stations * sc.G * round(sc.fs * sc.tint) * synth.integrations(sc) for sc in mix)
+
+    def jobs(prec):
+        return [serve.Job(q, sc, 0.0, precision=prec) for q, sc in enumerate(mix)]
+
+    ex = serve.GpuExecutor(corr, dev, pool, TC, tuner=tuner, copy_results=False)
+    sch = serve.Scheduler(ex, args.hbm_cap, args.hbm_reserve, fixed=pool.nbytes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = sch.run(jobs(TC))
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t_scan = serve.serial_run(corr, dev, pool, jobs(TC), TC, tuner=tuner)
+    t_fp32 = serve.serial_run(corr, dev, pool, jobs(corr.CORR_PREC_FP32), corr.CORR_PREC_FP32)
+    del pool
+    torch.cuda.empty_cache()
+    return {"workload": "cfg4: %d scans, 2-20 stations, 1-16 subbands, 1-2 pols, 128-8192 channels, 0.5-30 s, "
+                        "integrations <= 1 s" % len(mix),
+            "station_samples": samples, "integrations": sum(synth.integrations(sc) for sc in mix),
+            "value": samples / t_batch, "unit": METRIC, "seconds": t_batch,
+            "graph_launches": st["steps"], "max_scans_per_graph": st["max_batch"],
+            "peak_job_bytes": st["peak_bytes"], "per_scan_tc": {"value": samples / t_scan, "seconds": t_scan},
+            "serial_fp32": {"value": samples / t_fp32, "seconds": t_fp32},
+            "batched_vs_per_scan": t_scan / t_batch, "batched_tc_vs_serial_fp32": t_fp32 / t_batch,
+            "autotune": {"seconds": tune_s, "trials": tuner.trials, "shapes": len(tuner.cache),
+                         "chunk_blocks_chosen": sorted(set(tuner.cache.values()))},
+            "timing": "wall clock around the whole run, synchronised, handle set-up included",
+            "data": "device-resident random 2-bit pool, per-station offsets (replayed chunk)"}
+
+
+def serve_leg(args, torch, corr, dev):
+    """Poisson arrivals drawn from the uneven scan mix, admission by HBM
+    budget, continuous batching (one graph per step over all admitted jobs,
+    FP16 tensor-core X step), every integration read back to pinned host
+    memory; latency from arrival to the last integration on the host.  The
+    same arrivals are then served one job at a time through plain FP32."""
+    import synth
+    from paper_1502_06894_gb300 import serve
+    arr = serve.poisson_arrivals(args.serve_rate, args.serve_window, seed=5)
+    mix = synth.scan_mix(seed=5, count=max(1, len(arr)))
+    need = max(max(sc.nsamp) * sc.G // 4 for sc in mix)
+    pool = serve.ReplayPool(need + (64 << 20), dev, seed=5)
+    out = {}
+    for name, prec, plain, maxa in (("batched_tc", corr.CORR_PREC_FP16_TC, False, None),
+                                    ("serial_fp32", corr.CORR_PREC_FP32, True, 1)):
+        jobs = [serve.Job(q, sc, t, precision=prec) for q, (sc, t) in enumerate(zip(mix, arr))]
+        ex = serve.GpuExecutor(corr, dev, pool, prec, plain=plain)
+        sch = serve.Scheduler(ex, args.hbm_cap, args.hbm_reserve, fixed=pool.nbytes, max_active=maxa)
+        torch.cuda.synchronize()
+        st = sch.run(jobs)
+        out[name] = {"p50_s": st["p50_s"], "p99_s": st["p99_s"], "value": st["station_samples_per_s"],
+                     "unit": METRIC, "jobs": st["jobs"], "steps": st["steps"], "max_batch": st["max_batch"],
+                     "peak_job_bytes": st["peak_bytes"], "makespan_s": st["makespan_s"]}
+    offered = sum(sc.stations * sc.G * round(sc.fs * sc.tint) * synth.integrations(sc) for sc in mix)
+    del pool
+    torch.cuda.empty_cache()
+    return {"workload": "cfg5 shortened: Poisson %.0f jobs/s for %.1f s (the named run is 120 s), cfg4 shape mix, "
+                        "HBM cap %.0f GB, reserve %.0f GB" % (args.serve_rate, args.serve_window,
+                                                              args.hbm_cap / 1e9, args.hbm_reserve / 1e9),
+            "offered": offered / args.serve_window, "jobs": len(arr), **out,
+            "latency": "arrival to last integration in pinned host memory, wall clock"}
 
 
 def main():
@@ -481,6 +573,17 @@ def main():
                     "mode": "copy: corr_push_samples_async pieces two integrations ahead"}
         c3.close()
 
+    batch = None
+    served = None
+    if rank == 0 and ws == 1:
+        # free the single-scan buffers first: the mix brings its own pool
+        del out, wts
+        torch.cuda.empty_cache()
+        if not args.no_batch:
+            batch = batch_leg(args, torch, corr, dev)
+        if not args.no_serve:
+            served = serve_leg(args, torch, corr, dev)
+
     # ---- CPU oracle on a bounded sample ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -501,7 +604,8 @@ def main():
                            "chunk_blocks": cb, "x_partials": kz,
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "e2e_copy": e2e_copy}
+                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "e2e_copy": e2e_copy,
+                "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -104,6 +105,7 @@ struct corr_s {
   int* h_err = nullptr;  // pinned
   unsigned char* d_tiles = nullptr;  // tensor-core operand tiles (FFT length <= 2048)
   bool tc_tiles = false;
+  bool tc_direct = false;  // the F step writes the tiles itself
 
   // optional per-stage CUDA-event timing of the launches
   bool profiling = false;
@@ -264,7 +266,7 @@ static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
 struct WorkLayout {
   int64_t spi = 0;
   int Mcap = 0, CB = 0, KZ = 0, KZ_tc = 0, kz_alloc = 0;
-  bool tiles = false;
+  bool tiles = false, direct = false;
   size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;
   size_t total() const { return spec + part + tiles_bytes + small; }
 };
@@ -278,16 +280,29 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   const size_t nbl = (size_t)nbl_of(S);
   w.Mcap = (int)((w.spi + h->N - 1) / h->N) + 1;
   const size_t per_block = (size_t)G * S * nch * sizeof(float2);
+  const bool tc = h->precision == CORR_PREC_FP16_TC;
   int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
+  if (h->chunk_req <= 0) {
+    // Every chunk reads and writes all partial visibilities once; chunks of at
+    // least 32 (S + 1) / b blocks (b = bytes per complex spectrum value) keep
+    // that traffic near a quarter of the spectra the X step reads.  Up to four
+    // times the spectra budget is spent on that.
+    const int64_t want = (tc ? 8 : 4) * (int64_t)(S + 1);
+    const int64_t cap = (int64_t)(4 * h->spec_budget / per_block);
+    if (cb < want) cb = std::min(want, std::max(cap, cb));
+  }
   if (cb < 1) cb = 1;
   if (cb > w.Mcap) cb = w.Mcap;
   w.CB = (int)cb;
   w.KZ = xstage_kz(w.CB, S, G, nch);
   w.KZ_tc = (w.CB + kTcBlocks - 1) / kTcBlocks;
   w.kz_alloc = w.KZ > w.KZ_tc ? w.KZ : w.KZ_tc;
-  w.tiles = h->precision == CORR_PREC_FP16_TC && fstage_tc_tiles_supported(nch);
-  // in tile mode the F step writes the operand tiles, not a spectra buffer
-  w.spec = w.tiles ? 16 : per_block * w.CB;
+  // tensor-core operand tiles hold up to 64 stations; for FFTs of up to 2048
+  // points the F step writes them directly, above that FP16 spectra are
+  // corner-turned into them
+  w.tiles = tc && xtc_cpt(S) > 0;
+  w.direct = w.tiles && fstage_tc_tiles_supported(nch);
+  w.spec = w.direct ? 16 : (w.tiles ? per_block / 2 * w.CB : per_block * w.CB);
   w.part = sizeof(float2) * (size_t)w.kz_alloc * nbl * G * nch;
   if (w.tiles) {
     const int W = 2 * xtc_cpt(S);
@@ -346,6 +361,7 @@ static int prepare(corr_t* h) {
   if ((rc = dalloc(h, (void**)&h->d_err, sizeof(int), "error flag"))) return rc;
   CK(cudaMallocHost((void**)&h->h_err, sizeof(int)), "cudaMallocHost err");
   h->tc_tiles = w.tiles;
+  h->tc_direct = w.direct;
   if (h->tc_tiles) {
     if ((rc = dalloc(h, (void**)&h->d_tiles, w.tiles_bytes, "operand tiles"))) return rc;
     // rows beyond the stations of a tile stay zero for good
@@ -477,7 +493,8 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
       fp.scale = ldexpf(1.0f, -h->sigma);
     }
     if (h->tc_tiles) {
-      // F writes MMA operand tiles; X fetches them with bulk copies
+      // MMA operand tiles, fetched by the X step with bulk copies: written by
+      // the F step itself, or corner-turned from FP16 spectra
       TcTiles o;
       o.tiles = h->d_tiles;
       o.cpt = xtc_cpt(S);
@@ -486,7 +503,13 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
       o.NKT = (cb + 63) / 64;
       o.scale = ldexpf(1.0f, -h->sigma);
       pa = prof_begin(h);
-      CK(launch_fstage_tc(fp, o, st), "tensor-core fstage launch");
+      if (h->tc_direct) {
+        CK(launch_fstage_tc(fp, o, st), "tensor-core fstage launch");
+      } else {
+        CK(launch_fstage(fp, st), "fstage launch");
+        CK(launch_tiles(reinterpret_cast<const __half2*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
+           "tile corner-turn launch");
+      }
       prof_end(h, 1, pa);
       XTC2Params xp;
       xp.tiles = h->d_tiles;

@@ -127,6 +127,9 @@ int xtc_cpt(int S);
 bool fstage_tc_tiles_supported(int nchan);
 cudaError_t launch_fstage_tc(const FParams& p, const TcTiles& o, cudaStream_t s);
 cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s);
+// FP16 spectra [G][CB][S][nchan] (blocks < cb present) -> operand tiles
+cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
+                         cudaStream_t s);
 size_t xtc_smem_bytes(int S);
 cudaError_t launch_xtc(const XTCParams& p, int sm_count, cudaStream_t s);
 // finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale

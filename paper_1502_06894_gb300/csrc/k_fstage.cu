@@ -223,7 +223,13 @@ __device__ __forceinline__ void load_pair(const uint32_t* __restrict__ wsl, int 
   }
 }
 
-template <int L> struct MinBlocks { static constexpr int v = (L >= 512 && L <= 1024) ? 2 : 1; };
+// CTAs per SM the register allocation must allow: larger FFTs run one group
+// of 128-256 threads per FFT, so without a bound the compiler takes up to
+// 255 registers and a single CTA fills the SM's register file.  (8192 points
+// keep one CTA: the staged windows then fill shared memory anyway.)
+template <int L> struct MinBlocks {
+  static constexpr int v = (L >= 512 && L <= 1024) ? 2 : (L == 2048 ? 3 : (L == 4096 ? 2 : 1));
+};
 
 template <int L, int GC>
 __global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)

@@ -492,6 +492,79 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Corner turn of FP16 spectra into operand tiles, for FFT lengths at which
+// the F step cannot hold 8 blocks of spectra in shared memory.  One CTA takes
+// CH channels of one stream and one 64-block K tile; per 8-block K chunk it
+// reads the spectra of all stations (CH contiguous half2 per block and
+// station), then writes, for each (channel, station, Re/Im) row, the 8 blocks
+// as one 16-byte chunk of the 128-byte swizzled row.  All 8 chunks of a row
+// come from the same CTA, so each 128-byte line is complete while in L2.
+// Blocks at or beyond cb are written as zeros (the MMA reads whole K tiles).
+__global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec, TcTiles o, int CB, int cb, int S,
+                                               int nchan, int CH) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __half2* st = reinterpret_cast<__half2*>(smem_raw);  // [8][S][CH]
+  const int c0 = blockIdx.x * CH;
+  const int kt = blockIdx.y;
+  const int jo = blockIdx.z;
+  const int nch = min(CH, nchan - c0);
+  const int tid = threadIdx.x;
+  for (int kc = 0; kc < 8; ++kc) {
+    const int b0 = kt * 64 + kc * 8;
+    // stage: rows (e, s) of nch channels
+    for (int i = tid; i < 8 * S * CH; i += blockDim.x) {
+      const int c = i % CH;
+      const int es = i / CH;
+      const int s = es % S, e = es / S;
+      const int b = b0 + e;
+      __half2 v = __floats2half2_rn(0.f, 0.f);
+      if (c < nch && b < cb) v = spec[(((size_t)jo * CB + b) * S + s) * (size_t)nchan + c0 + c];
+      st[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < S * nch; i += blockDim.x) {
+      const int c = i / S;
+      const int s = i - c * S;
+      uint32_t re[4], im[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const __half2 a = st[((size_t)e * S + s) * CH + c];
+        const __half2 b = st[((size_t)(e + 1) * S + s) * CH + c];
+        re[e / 2] = (uint32_t)__half_as_ushort(__low2half(a)) | ((uint32_t)__half_as_ushort(__low2half(b)) << 16);
+        im[e / 2] = (uint32_t)__half_as_ushort(__high2half(a)) | ((uint32_t)__half_as_ushort(__high2half(b)) << 16);
+      }
+      const int k = c0 + c;
+      const int sl = k / o.W;
+      const int cw = k - sl * o.W;
+      const int tg = cw / o.cpt;
+      const int cl = cw - tg * o.cpt;
+      const int r = (cl * S + s) * 2;
+      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+      *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
+          make_uint4(re[0], re[1], re[2], re[3]);
+      const int r1 = r + 1;
+      *reinterpret_cast<uint4*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4)) =
+          make_uint4(im[0], im[1], im[2], im[3]);
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
+                         cudaStream_t s) {
+  if (cb <= 0) return cudaSuccess;
+  // channels per CTA: the 8-block staging area stays within 48 KB
+  int CH = 32 * ((48 * 1024 / (8 * 4 * S)) / 32);
+  if (CH < 32) CH = 32;
+  if (CH > 256) CH = 256;
+  const size_t smem = (size_t)8 * S * CH * sizeof(__half2);
+  cudaError_t e = cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nchan + CH - 1) / CH, o.NKT, G);
+  k_tiles<<<grid, 256, smem, s>>>(spec, o, CB, cb, S, nchan, CH);
+  return cudaGetLastError();
+}
+
 int xtc_cpt(int S) { return S <= 64 ? 64 / S : 0; }
 
 size_t xtc_smem_bytes(int S) {

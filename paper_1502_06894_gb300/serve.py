@@ -293,8 +293,9 @@ class GpuExecutor:
 
     def __init__(self, corr_mod, device, pool: ReplayPool, precision: int,
                  on_result: Optional[Callable] = None, tuner: Optional[Autotuner] = None,
-                 chunk_blocks: Optional[int] = None, copy_results: bool = True):
+                 chunk_blocks: Optional[int] = None, copy_results: bool = True, plain: bool = False):
         import torch
+        self.plain = plain  # one corr_correlate_device per job instead of one graph per step
         self.corr = corr_mod
         self.dev = device
         self.pool = pool
@@ -344,8 +345,15 @@ class GpuExecutor:
         import torch
         t0 = time.perf_counter()
         sts = [self.state[j.jid] for j in jobs]
-        self.corr.batch_run([s["c"] for s in sts], [s["out"] for s in sts], [s["w"] for s in sts],
-                            stream=self.stream.cuda_stream)
+        if self.plain:
+            for s in sts:
+                rc = s["c"].correlate_device(s["out"], s["w"])
+                if rc != self.corr.CORR_OK:
+                    raise RuntimeError("correlate_device returned %d" % rc)
+            torch.cuda.synchronize()
+        else:
+            self.corr.batch_run([s["c"] for s in sts], [s["out"] for s in sts], [s["w"] for s in sts],
+                                stream=self.stream.cuda_stream)
         if self.copy_results:
             with torch.cuda.stream(self.stream):
                 for s in sts:

@@ -82,10 +82,14 @@ def test_tc_64_stations(corr):
     check(sc, vis, w, ref, wref, 2, "64 stations")
 
 
-@pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (128, 33, 1, 1)])
+@pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (128, 33, 1, 1),
+                                               (2048, 5, 3, 1), (64, 65, 1, 1)])
 def test_tc_shapes(corr, nchan, S, nsub, npol):
     """Tiles of 32, 21, 9 and 1 channels, odd stream counts, a slice wider
-    than the band, 8-byte copies."""
+    than the band, 8-byte copies; 4096-point FFTs whose FP16 spectra are
+    corner-turned into tiles (12 channels per tile pair, a ragged last
+    corner-turn CTA); 65 stations, beyond one tile, on the transposing
+    tensor-core kernel."""
     fs = 32e6
     N = 2 * nchan
     tint = round((300 * N + 5) / fs * fs) / fs
