@@ -19,7 +19,6 @@ using namespace corr;
 
 constexpr int kStages = 4;  // delay blocks, F, X, weights+finalise
 // blocks accumulated in tensor memory (FP32) before the partial sum in HBM
-constexpr int kTcBlocks = 1024;
 
 namespace {
 
@@ -99,7 +98,6 @@ struct corr_s {
   size_t spec_budget = (size_t)1 << 30;
   int chunk_req = 0;  // blocks per F/X chunk requested by the caller (0: from spec_budget)
   int sm_count = 0;
-  int KZ_tc = 0;      // tensor-core partial sums per chunk (<= 256 blocks each)
   int sigma = 0;      // FP16 spectra carry X * 2^-sigma
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned
@@ -265,7 +263,7 @@ static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
 // allocation and by the memory estimate a scheduler asks for).
 struct WorkLayout {
   int64_t spi = 0;
-  int Mcap = 0, CB = 0, KZ = 0, KZ_tc = 0, kz_alloc = 0;
+  int Mcap = 0, CB = 0, KZ = 0;
   bool tiles = false, direct = false;
   size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;
   size_t total() const { return spec + part + tiles_bytes + small; }
@@ -295,15 +293,14 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   if (cb > w.Mcap) cb = w.Mcap;
   w.CB = (int)cb;
   w.KZ = xstage_kz(w.CB, S, G, nch);
-  w.KZ_tc = (w.CB + kTcBlocks - 1) / kTcBlocks;
-  w.kz_alloc = w.KZ > w.KZ_tc ? w.KZ : w.KZ_tc;
   // tensor-core operand tiles hold up to 64 stations; for FFTs of up to 2048
   // points the F step writes them directly, above that FP16 spectra are
   // corner-turned into them
   w.tiles = tc && xtc_cpt(S) > 0;
   w.direct = w.tiles && fstage_tc_tiles_supported(nch);
   w.spec = w.direct ? 16 : (w.tiles ? per_block / 2 * w.CB : per_block * w.CB);
-  w.part = sizeof(float2) * (size_t)w.kz_alloc * nbl * G * nch;
+  // partial sums: KZ slices for the FP32 X step, one for the tensor cores
+  w.part = sizeof(float2) * (size_t)(tc ? 1 : w.KZ) * nbl * G * nch;
   if (w.tiles) {
     const int W = 2 * xtc_cpt(S);
     w.tiles_bytes = (size_t)G * ((nch + W - 1) / W) * ((size_t)(w.CB + 63) / 64) * 32768;
@@ -333,7 +330,6 @@ static int prepare(corr_t* h) {
   h->Mcap = w.Mcap;
   h->CB = w.CB;
   h->KZ = w.KZ;
-  h->KZ_tc = w.KZ_tc;
   {
     int lg = 0;
     while ((1 << (lg + 1)) <= h->N) ++lg;
@@ -481,7 +477,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
   cudaEvent_t pa = nullptr;
   // F and X per chunk
   const int nbl = nbl_of(S);
-  const int kz_used = h->precision == CORR_PREC_FP16_TC ? (h->tc_tiles ? 1 : h->KZ_tc) : h->KZ;
+  const int kz_used = h->precision == CORR_PREC_FP16_TC ? 1 : h->KZ;
   CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, st),
      "partials memset");
   const bool tc = h->precision == CORR_PREC_FP16_TC;
@@ -530,23 +526,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
     pa = prof_begin(h);
     CK(launch_fstage(fp, st), "fstage launch");
     prof_end(h, 1, pa);
-    if (tc) {
-      XTCParams xp;
-      xp.spec = reinterpret_cast<const __half2*>(h->d_spec);
-      xp.CB = cb;
-      xp.cb = cb;
-      xp.kblocks = kTcBlocks;
-      xp.S = S;
-      xp.G = h->G;
-      xp.nchan = h->nchan;
-      xp.cpt = xtc_cpt(S);
-      xp.W = 2 * xp.cpt;
-      xp.part = h->d_part;
-      xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xtc(xp, h->sm_count, st), "tensor-core xstage launch");
-      prof_end(h, 2, pa);
-    } else {
+    {
       XParams xp;
       xp.spec = h->d_spec;
       xp.CB = cb;

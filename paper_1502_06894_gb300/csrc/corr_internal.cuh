@@ -80,19 +80,6 @@ struct XTC2Params {
   int* err;
 };
 
-// X step on tensor cores: FP16 spectra in, FP32 partial sums out.
-struct XTCParams {
-  const __half2* spec;      // [G][CB][S][nchan]
-  int CB;                   // blocks per stream in the spectra buffer
-  int cb;                   // blocks present in this chunk
-  int kblocks;              // blocks per partial sum (a multiple of 64)
-  int S, G, nchan;
-  int cpt;                  // channels per 128-row tile (floor(64/S))
-  int W;                    // channels per work item (2 * cpt)
-  float2* part;             // [KZ][G][nchan][nbl], KZ = ceil(cb / kblocks)
-  int* err;                 // set to 1 when a device wait times out
-};
-
 // X stage: V_ab[k] += X_a[k] conj(X_b[k]) over the chunk's blocks.
 struct XParams {
   const float2* spec;       // [G][CB][S][nchan]
@@ -130,8 +117,6 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s);
 // FP16 spectra [G][CB][S][nchan] (blocks < cb present) -> operand tiles
 cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
                          cudaStream_t s);
-size_t xtc_smem_bytes(int S);
-cudaError_t launch_xtc(const XTCParams& p, int sm_count, cudaStream_t s);
 // finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale
 cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s);
 

@@ -11,15 +11,11 @@
 // across different channels are computed and discarded.  A = B = the same
 // shared-memory tile.
 //
-// Data path of a persistent CTA (128 threads, one per SM):
-//   global FP16 spectra [stream][block][station][channel] (the F step's output)
-//   --cp.async, 3 stages--> shared staging, natural layout, one 64-block K tile
-//   of a slice of W = 2*cpt channels
-//   --threads--> two 128 x 64 operand tiles, K-major, 128-byte swizzle
-//   --tcgen05.mma, issued by one thread--> two 128 x 128 FP32 accumulators in
-//   TMEM (256 columns), accumulated over the item's K tiles (<= 1024 blocks)
-//   --tcgen05.ld + lane shuffle (Re/Im rows are neighbouring lanes)-->
-//   V_ab added to an FP32 partial sum in global memory (fixed order).
+// Operand tiles: 128 rows x 64 blocks of FP16, K-major with the 128-byte
+// swizzle, written by the F step (directly, or by the corner turn k_tiles
+// from FP16 spectra); the X kernel k_xmma2 streams them with bulk copies into
+// shared memory, issues the MMAs into TMEM accumulators and adds V_ab into
+// FP32 partial sums in global memory.
 // Every wait on an mbarrier is bounded; on timeout the CTA sets *err, stops
 // issuing work, waits for its own copies, frees its TMEM and returns.
 #include "corr_internal.cuh"
@@ -30,34 +26,12 @@ namespace corr {
 
 namespace {
 
-constexpr int kThreads = 128;
 constexpr int kKT = 64;            // blocks per K tile (64 FP16 = one 128-byte swizzle row)
-constexpr int kStages = 3;
 constexpr int kTileBytes = 128 * kKT * 2;  // one 128-row operand tile
 constexpr long kWaitLimit = 1L << 26;      // spins before an mbarrier wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes, int src_bytes) {
-  if (bytes == 16)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok = 0;
-  for (long it = 0; it < kWaitLimit; ++it) {
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
 }
 
 // K-major operand tile, 128-byte swizzle: element (row r, k) of a 128 x 64
@@ -95,218 +69,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-struct Cursor {
-  int item;  // global item index (valid while < nitems)
-  int kt;    // K tile within the item
-};
-
 }  // namespace
-
-__global__ void __launch_bounds__(kThreads, 1) k_xmma(XTCParams p, int nitems, int stage_bytes) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // operand tiles first, on a 1024-byte boundary (the 128-byte swizzle is a
-  // function of the address bits), then the staging ring
-  const uint32_t raw = smem_u32(smem_raw);
-  unsigned char* opnd = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // [2 buf][2 grp][16 KB]
-  unsigned char* stage = opnd + 4 * kTileBytes;                        // [kStages][stage_bytes]
-  __shared__ __align__(8) uint64_t s_mma_done[2];
-  __shared__ uint32_t s_taddr;
-  __shared__ int s_abort;
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = p.S, W = p.W, cpt = p.cpt, G = p.G, nchan = p.nchan;
-  const int nslice = (nchan + W - 1) / W;
-  const int rows_valid = 2 * S * cpt;
-  const int nbl = nbl_of(S);
-  const int chunk = (W * 4) % 16 == 0 ? 16 : 8;       // cp.async size
-  const int cpr = W * 4 / chunk;                        // chunks per (block, station) row
-  const size_t rowpitch = (size_t)nchan;               // half2 elements per (block, station)
-
-  // zero both operand buffers once: rows >= rows_valid stay zero
-  for (int q = tid; q < 4 * kTileBytes / 16; q += kThreads)
-    reinterpret_cast<uint4*>(opnd)[q] = make_uint4(0, 0, 0, 0);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mma_done[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mma_done[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&s_taddr)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = s_taddr;
-
-  auto ntiles = [&](int item) {
-    const int kz = item / (G * nslice);
-    const int b0 = kz * p.kblocks;
-    int b1 = b0 + p.kblocks;
-    if (b1 > p.cb) b1 = p.cb;
-    return (b1 - b0 + kKT - 1) / kKT;
-  };
-  auto advance = [&](Cursor& c) {
-    if (++c.kt >= ntiles(c.item)) {
-      c.kt = 0;
-      c.item += gridDim.x;
-    }
-  };
-  // issue the copies of tile (item, kt) into stage buffer sb
-  auto issue = [&](const Cursor& c, int sb) {
-    if (c.item < nitems) {
-      const int kz = c.item / (G * nslice);
-      const int rem = c.item - kz * G * nslice;
-      const int g = rem / nslice;
-      const int c0 = (rem - g * nslice) * W;
-      const int b0 = kz * p.kblocks + c.kt * kKT;
-      int bend = kz * p.kblocks + p.kblocks;
-      if (bend > p.cb) bend = p.cb;
-      const uint32_t sbase = smem_u32(stage + sb * stage_bytes);
-      const int total = kKT * S * cpr;
-      for (int q = tid; q < total; q += kThreads) {
-        const int row = q / cpr;                 // row = b * S + s
-        const int part = q - row * cpr;
-        const int b = row / S;
-        const int s = row - b * S;
-        const int ch = c0 + part * (chunk / 4);
-        const bool in = (b0 + b) < bend && ch < nchan;
-        const __half2* src = p.spec + (((size_t)g * p.CB + (in ? b0 + b : 0)) * S + s) * rowpitch + (in ? ch : 0);
-        cp_async(sbase + (uint32_t)(row * W * 4 + part * chunk), src, chunk, in ? chunk : 0);
-      }
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-
-  Cursor cur{(int)blockIdx.x, 0};
-  Cursor pre = cur;
-  issue(pre, 0);
-  advance(pre);
-  issue(pre, 1);
-  advance(pre);
-
-  uint32_t t = 0;  // tiles processed by this CTA
-  while (cur.item < nitems) {
-    issue(pre, (t + 2) % kStages);
-    advance(pre);
-    asm volatile("cp.async.wait_group 2;" ::: "memory");
-    __syncthreads();
-    if (s_abort) break;
-
-    const int buf = t & 1;
-    if (t >= 2 && !mbar_wait(&s_mma_done[buf], ((t - 2) >> 1) & 1)) s_abort = 1;
-    __syncthreads();
-    if (s_abort) break;
-
-    // ---- transpose staging (natural [b][s][c], half2) -> two swizzled operand tiles ----
-    {
-      const __half2* st = reinterpret_cast<const __half2*>(stage + (t % kStages) * stage_bytes);
-      // unit = (8-block chunk kc, station s, channel gc of the slice), gc fastest
-      // so that a warp's reads of the staging are consecutive words
-      const int units = 2 * cpt * S * 8;
-      for (int u = tid; u < units; u += kThreads) {
-        const int gc = u % W;                // group * cpt + channel-in-group
-        const int rest = u / W;
-        const int s = rest % S;
-        const int kc = rest / S;
-        const int grp = gc / cpt;
-        const int cl = gc - grp * cpt;
-        uint32_t re[4], im[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          const __half2 x0 = st[((kc * 8 + e) * S + s) * W + gc];
-          const __half2 x1 = st[((kc * 8 + e + 1) * S + s) * W + gc];
-          re[e / 2] = (uint32_t)__half_as_ushort(__low2half(x0)) | ((uint32_t)__half_as_ushort(__low2half(x1)) << 16);
-          im[e / 2] = (uint32_t)__half_as_ushort(__high2half(x0)) | ((uint32_t)__half_as_ushort(__high2half(x1)) << 16);
-        }
-        const int r = (cl * S + s) * 2;
-        unsigned char* tile = opnd + (buf * 2 + grp) * kTileBytes;
-        *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
-            make_uint4(re[0], re[1], re[2], re[3]);
-        const int r1 = r + 1;
-        *reinterpret_cast<uint4*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4)) =
-            make_uint4(im[0], im[1], im[2], im[3]);
-      }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-
-    // ---- MMAs: 2 groups x 4 K steps of 16 ----
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      for (int grp = 0; grp < 2; ++grp) {
-        const uint64_t d0 = sw128_desc(smem_u32(opnd + (buf * 2 + grp) * kTileBytes));
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-          mma_f16(taddr + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (cur.kt > 0 || ks > 0) ? 1u : 0u);
-      }
-      mma_commit(&s_mma_done[buf]);
-    }
-
-    // ---- end of an item: read the accumulators and add V to the partial sums ----
-    const bool last = (cur.kt + 1 >= ntiles(cur.item));
-    if (last) {
-      if (!mbar_wait(&s_mma_done[buf], (t >> 1) & 1)) s_abort = 1;
-      __syncthreads();
-      if (s_abort) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int kz = cur.item / (G * nslice);
-      const int rem = cur.item - kz * G * nslice;
-      const int g = rem / nslice;
-      const int c0 = (rem - g * nslice) * W;
-      const int r = warp * 32 + lane;
-      const bool re_lane = ((lane & 1) == 0) && r < rows_valid;
-      const int a = (r >> 1) % S;
-      const int cl = (r >> 1) / S;
-      // this warp's rows hold channels cmin..cmax of each group: only their
-      // diagonal blocks of the accumulator are read
-      int rlast = warp * 32 + 31;
-      if (rlast > rows_valid - 1) rlast = rows_valid - 1;
-      const int cmin = (warp * 32) / (2 * S), cmax = rlast / (2 * S);
-      const int q0 = (2 * S * cmin) / 32, q1 = (warp * 32 < rows_valid) ? (2 * S * (cmax + 1) - 1) / 32 : -1;
-#pragma unroll 1
-      for (int grp = 0; grp < 2; ++grp) {
-        const int k = c0 + grp * cpt + cl;
-        float2* dst = p.part + (((size_t)kz * G + g) * nchan + (k < nchan ? k : 0)) * nbl;
-        const bool mine = re_lane && k < nchan;
-#pragma unroll 1
-        for (int q = q0; q <= q1; ++q) {
-          uint32_t v[32];
-          tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + grp * 128 + q * 32, v);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float m0 = __uint_as_float(v[2 * i]), m1 = __uint_as_float(v[2 * i + 1]);
-            const float n0 = __shfl_down_sync(0xffffffffu, m0, 1);
-            const float n1 = __shfl_down_sync(0xffffffffu, m1, 1);
-            const int j = q * 32 + 2 * i;      // column of (station b, Re)
-            const int clj = (j >> 1) / S;
-            const int b = (j >> 1) % S;
-            if (mine && clj == cl && b >= a) {
-              // each partial-sum element gets exactly one add per launch, so a
-              // fire-and-forget reduction keeps the sums deterministic
-              float* o = reinterpret_cast<float*>(dst + bl_index(a, b, S));
-              atomicAdd(o, m0 + n1);
-              atomicAdd(o + 1, n0 - m1);
-            }
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();
-    }
-    ++t;
-    advance(cur);
-  }
-
-  // ---- teardown: no copies in flight, TMEM freed ----
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  if (s_abort && tid == 0) atomicExch(p.err, 1);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(taddr));
-}
 
 // ---------------------------------------------------------------------------
 // k_xmma2: the X step from ready-made operand tiles (written by the tensor-core
@@ -349,7 +112,7 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = p.S, cpt = p.cpt, W = p.W, G = p.G, nchan = p.nchan, NKT = p.NKT;
+  const int S = p.S, cpt = p.cpt, W = p.W, nchan = p.nchan, NKT = p.NKT;
   const int nbl = nbl_of(S);
   const int rows_valid = 2 * S * cpt;
 
@@ -502,8 +265,8 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
 // Blocks at or beyond cb are written as zeros (the MMA reads whole K tiles).
 __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec, TcTiles o, int CB, int cb, int S,
                                                int nchan, int CH) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __half2* st = reinterpret_cast<__half2*>(smem_raw);  // [8][S][CH]
+  extern __shared__ __align__(16) unsigned char turn_raw[];
+  __half2* st = reinterpret_cast<__half2*>(turn_raw);  // [8][S][CH]
   const int c0 = blockIdx.x * CH;
   const int kt = blockIdx.y;
   const int jo = blockIdx.z;
@@ -566,26 +329,5 @@ cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, 
 }
 
 int xtc_cpt(int S) { return S <= 64 ? 64 / S : 0; }
-
-size_t xtc_smem_bytes(int S) {
-  const int W = 2 * xtc_cpt(S);
-  const size_t stage = (size_t)kKT * S * W * 4;
-  return 1024 + 4 * (size_t)kTileBytes + kStages * ((stage + 1023) & ~(size_t)1023);
-}
-
-cudaError_t launch_xtc(const XTCParams& p, int sm_count, cudaStream_t s) {
-  if (p.cb <= 0) return cudaSuccess;
-  const int nslice = (p.nchan + p.W - 1) / p.W;
-  const int kz = (p.cb + p.kblocks - 1) / p.kblocks;
-  const int nitems = kz * p.G * nslice;
-  const int stage_bytes = (int)(((size_t)kKT * p.S * p.W * 4 + 1023) & ~(size_t)1023);
-  const size_t smem = 1024 + 4 * (size_t)kTileBytes + kStages * (size_t)stage_bytes;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-  cudaError_t e = cudaFuncSetAttribute(k_xmma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int grid = nitems < sm_count ? nitems : sm_count;
-  k_xmma<<<grid, kThreads, smem, s>>>(p, nitems, stage_bytes);
-  return cudaGetLastError();
-}
 
 }  // namespace corr

@@ -83,13 +83,12 @@ def test_tc_64_stations(corr):
 
 
 @pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (128, 33, 1, 1),
-                                               (2048, 5, 3, 1), (64, 65, 1, 1)])
+                                               (2048, 5, 3, 1), (32, 64, 1, 1)])
 def test_tc_shapes(corr, nchan, S, nsub, npol):
     """Tiles of 32, 21, 9 and 1 channels, odd stream counts, a slice wider
     than the band, 8-byte copies; 4096-point FFTs whose FP16 spectra are
     corner-turned into tiles (12 channels per tile pair, a ragged last
-    corner-turn CTA); 65 stations, beyond one tile, on the transposing
-    tensor-core kernel."""
+    corner-turn CTA); 64 stations, one channel per tile."""
     fs = 32e6
     N = 2 * nchan
     tint = round((300 * N + 5) / fs * fs) / fs
@@ -99,6 +98,14 @@ def test_tc_shapes(corr, nchan, S, nsub, npol):
     ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
     vis, w = run_tc(corr, sc, streams, 2)
     check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d" % (S, nchan, nsub * npol))
+
+
+def test_tc_rejects_more_than_64_stations(corr):
+    c = corr.Correlator(65, 1, 1, 64, 0.001)
+    with pytest.raises(corr.CorrError) as ei:
+        c.set_precision(corr.CORR_PREC_FP16_TC)
+    assert ei.value.code == corr.CORR_EINVAL
+    c.close()
 
 
 def test_tc_two_bit_efficiency_config1(corr, cfg1):
