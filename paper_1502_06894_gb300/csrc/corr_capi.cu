@@ -283,9 +283,10 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   if (h->chunk_req <= 0) {
     // Every chunk reads and writes all partial visibilities once; chunks of at
     // least 32 (S + 1) / b blocks (b = bytes per complex spectrum value) keep
-    // that traffic near a quarter of the spectra the X step reads.  Up to four
-    // times the spectra budget is spent on that.
-    const int64_t want = (tc ? 8 : 4) * (int64_t)(S + 1);
+    // that traffic near a quarter of the spectra the X step reads.  On the
+    // tensor cores a chunk of 512 blocks also gives each accumulator 8 K tiles
+    // before its read-out.  Up to four times the spectra budget is spent on it.
+    const int64_t want = tc ? std::max<int64_t>(8 * (int64_t)(S + 1), 512) : 4 * (int64_t)(S + 1);
     const int64_t cap = (int64_t)(4 * h->spec_budget / per_block);
     if (cb < want) cb = std::min(want, std::max(cap, cb));
   }

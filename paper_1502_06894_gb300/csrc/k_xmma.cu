@@ -257,70 +257,87 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
 
 // Corner turn of FP16 spectra into operand tiles, for FFT lengths at which
 // the F step cannot hold 8 blocks of spectra in shared memory.  One CTA takes
-// CH channels of one stream and one 64-block K tile; per 8-block K chunk it
-// reads the spectra of all stations (CH contiguous half2 per block and
-// station), then writes, for each (channel, station, Re/Im) row, the 8 blocks
-// as one 16-byte chunk of the 128-byte swizzled row.  All 8 chunks of a row
-// come from the same CTA, so each 128-byte line is complete while in L2.
+// CH channels of one stream and one 64-block K tile:
+//   stage   the spectra of all stations and the tile's 64 blocks, split into
+//           Re and Im rows of 64 FP16 values (one 128-byte tile row each, in
+//           block order; rows 144 bytes apart so that neighbouring channels
+//           fall in different banks), from 16-byte reads of 4 channels, four
+//           blocks per thread;
+//   write   8 threads per row, one 16-byte chunk each, to the chunk's swizzled
+//           place: every tile row is written as one whole 128-byte line.
 // Blocks at or beyond cb are written as zeros (the MMA reads whole K tiles).
+constexpr int kTurnRow = 144;  // bytes per staged row (64 FP16 + 16 bytes of padding)
+
 __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec, TcTiles o, int CB, int cb, int S,
                                                int nchan, int CH) {
-  extern __shared__ __align__(16) unsigned char turn_raw[];
-  __half2* st = reinterpret_cast<__half2*>(turn_raw);  // [8][S][CH]
+  extern __shared__ __align__(16) unsigned char turn_raw[];  // [Re/Im][S][CH] rows of kTurnRow bytes
   const int c0 = blockIdx.x * CH;
   const int kt = blockIdx.y;
   const int jo = blockIdx.z;
   const int nch = min(CH, nchan - c0);
   const int tid = threadIdx.x;
-  for (int kc = 0; kc < 8; ++kc) {
-    const int b0 = kt * 64 + kc * 8;
-    // stage: rows (e, s) of nch channels
-    for (int i = tid; i < 8 * S * CH; i += blockDim.x) {
-      const int c = i % CH;
-      const int es = i / CH;
-      const int s = es % S, e = es / S;
-      const int b = b0 + e;
-      __half2 v = __floats2half2_rn(0.f, 0.f);
-      if (c < nch && b < cb) v = spec[(((size_t)jo * CB + b) * S + s) * (size_t)nchan + c0 + c];
-      st[i] = v;
-    }
-    __syncthreads();
-    for (int i = tid; i < S * nch; i += blockDim.x) {
-      const int c = i / S;
-      const int s = i - c * S;
-      uint32_t re[4], im[4];
+  // staging: a thread takes 4 channels x 4 consecutive blocks of one station
+  // (four 16-byte loads in flight), and stores per channel the 4 Re and the
+  // 4 Im values as one 8-byte piece of each row.  Threads run over blocks
+  // fastest, so a half-warp fills 64-byte runs of two rows that sit in
+  // different banks (rows 4 apart are 576 bytes apart).
+  const int CV = CH / 4;
+  const int nstage = S * 2 * CV * 8;
+  for (int i = tid; i < nstage; i += blockDim.x) {
+    const int b4 = i & 7;
+    const int j = i >> 3;
+    const int c = 4 * (j % CV);
+    const int rest = j / CV;
+    const int bh = rest & 1;
+    const int sb = rest >> 1;
+    const int b0 = bh * 32 + b4 * 4;
+    uint4 v[4];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        const __half2 a = st[((size_t)e * S + s) * CH + c];
-        const __half2 b = st[((size_t)(e + 1) * S + s) * CH + c];
-        re[e / 2] = (uint32_t)__half_as_ushort(__low2half(a)) | ((uint32_t)__half_as_ushort(__low2half(b)) << 16);
-        im[e / 2] = (uint32_t)__half_as_ushort(__high2half(a)) | ((uint32_t)__half_as_ushort(__high2half(b)) << 16);
-      }
-      const int k = c0 + c;
-      const int sl = k / o.W;
-      const int cw = k - sl * o.W;
-      const int tg = cw / o.cpt;
-      const int cl = cw - tg * o.cpt;
-      const int r = (cl * S + s) * 2;
-      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
-      *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
-          make_uint4(re[0], re[1], re[2], re[3]);
-      const int r1 = r + 1;
-      *reinterpret_cast<uint4*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4)) =
-          make_uint4(im[0], im[1], im[2], im[3]);
+    for (int u = 0; u < 4; ++u) {
+      const int bg = kt * 64 + b0 + u;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (c < nch && bg < cb)
+        v[u] = __ldg(reinterpret_cast<const uint4*>(spec + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
     }
-    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w[u] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+      const uint2 re = make_uint2((w[0] & 0xFFFFu) | (w[1] << 16), (w[2] & 0xFFFFu) | (w[3] << 16));
+      const uint2 im = make_uint2((w[0] >> 16) | (w[1] & 0xFFFF0000u), (w[2] >> 16) | (w[3] & 0xFFFF0000u));
+      *reinterpret_cast<uint2*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 2 * b0) = re;
+      *reinterpret_cast<uint2*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 2 * b0) = im;
+    }
+  }
+  __syncthreads();
+  const int nitems = 2 * S * nch * 8;
+  for (int i = tid; i < nitems; i += blockDim.x) {
+    const int kc = i & 7;
+    const int row = i >> 3;  // (ri * S + s) * nch + c
+    const int c = row % nch;
+    const int rs = row / nch;
+    const int s = rs % S;
+    const int ri = rs / S;
+    const uint4 v = *reinterpret_cast<const uint4*>(turn_raw + ((size_t)rs * CH + c) * kTurnRow + kc * 16);
+    const int k = c0 + c;
+    const int sl = k / o.W;
+    const int cw = k - sl * o.W;
+    const int tg = cw / o.cpt;
+    const int cl = cw - tg * o.cpt;
+    const int r = (cl * S + s) * 2 + ri;
+    unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+    *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) = v;
   }
 }
 
 cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
                          cudaStream_t s) {
   if (cb <= 0) return cudaSuccess;
-  // channels per CTA: the 8-block staging area stays within 48 KB
-  int CH = 32 * ((48 * 1024 / (8 * 4 * S)) / 32);
-  if (CH < 32) CH = 32;
-  if (CH > 256) CH = 256;
-  const size_t smem = (size_t)8 * S * CH * sizeof(__half2);
+  // channels per CTA: the staged rows stay within about 100 KB
+  int CH = 16;
+  while (CH > 4 && (size_t)2 * S * CH * kTurnRow > 100 * 1024) CH /= 2;
+  const size_t smem = (size_t)2 * S * CH * kTurnRow;
   cudaError_t e = cudaFuncSetAttribute(k_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nchan + CH - 1) / CH, o.NKT, G);
