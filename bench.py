@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tc", action="store_true", help="skip the FP16 tensor-core leg")
+    ap.add_argument("--no-fp8", action="store_true", help="skip the FP8 tensor-core leg")
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--chunk-blocks", type=int, default=0, help="FFT blocks per F/X chunk (0: library default)")
     ap.add_argument("--duration", type=float, default=10.0,
@@ -411,6 +412,9 @@ def main():
     tc = None
     if not args.no_tc:
         ms_tc, prof_tc, clocks_tc, _ = device_leg(corr.CORR_PREC_FP16_TC)
+    fp8 = None
+    if not args.no_fp8:
+        ms_f8, prof_f8, clocks_f8, _ = device_leg(corr.CORR_PREC_FP8_TC)
 
     # ---- roofline of the dominant kernel ----
     peak_hbm, peak_src = measured_peaks()
@@ -447,7 +451,7 @@ def main():
         roof = {"bound": "alu", "achieved": tfl, "peak": peak_alu / 1e12, "unit": "TFLOP/s", "frac": alu_frac,
                 "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
     gc = G if G in (16, 32) else 0
-    kname = "k_fstage<%d,%d>" % (nch, gc) if dom == "fstage" else "k_xmac_ring<%d>" % S
+    kname = "k_fstage<%d,%d>" % (nch, gc) if dom == "fstage" else "k_xmac_tma<%d>" % S
     traffic = traffic_per_launch(kname)
     roof["traffic"] = traffic
     roof["traffic_over_algorithmic"] = (traffic / (d_bytes / max(d_n, 1))) if traffic else None
@@ -456,19 +460,27 @@ def main():
                  "launch_ms": t_launch * 1e3, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
     launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
+    def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound, measured):
+        xt_ms, xt_n = prof_t["xstage"]
+        ft_ms, ft_n = prof_t["fstage"]
+        # reduced-precision spectra: elem_bytes read per station-sample in the X step
+        xt_bytes = steps * ss_step * elem_bytes
+        return {"value": sps * ws / (ms_t / 1e3), "unit": METRIC, "ms_per_step": ms_t, "dtype": dtype,
+                "error_bound_rel_rms": bound, "measured_rel_rms": measured,
+                "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
+                "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
+                "xstep_hbm_gbs": xt_bytes / (xt_ms / 1e3) / 1e9 if xt_ms > 0 else None,
+                "xstep_vs_fp32_xstep": (x_ms / xt_ms) if xt_ms > 0 else None,
+                "stages": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
+                           for k, v in prof_t.items()},
+                "clocks": clocks_t}
+
     if not args.no_tc:
-        xt_ms, xt_n = prof_tc["xstage"]
-        ft_ms, ft_n = prof_tc["fstage"]
-        # FP16 spectra: 2 B read per station-sample in the X step
-        xt_bytes = steps * ss_step * 2.0
-        tc = {"value": sps * ws / (ms_tc / 1e3), "unit": METRIC, "ms_per_step": ms_tc, "dtype": "f16 in, f32 accumulate",
-              "error_bound_rel_rms": 1.5e-3, "measured_rel_rms": "3.0e-4 .. 3.5e-4 (GPU parity tests)",
-              "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
-              "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
-              "xstep_hbm_gbs": xt_bytes / (xt_ms / 1e3) / 1e9 if xt_ms > 0 else None,
-              "xstep_vs_fp32_xstep": (x_ms / xt_ms) if xt_ms > 0 else None,
-              "stages": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps} for k, v in prof_tc.items()},
-              "clocks": clocks_tc}
+        tc = tc_leg(ms_tc, prof_tc, clocks_tc, "f16 in, f32 accumulate", 2.0, 1.5e-3,
+                    "3.0e-4 .. 3.5e-4 (GPU parity tests)")
+    if not args.no_fp8:
+        fp8 = tc_leg(ms_f8, prof_f8, clocks_f8, "e4m3 in, f32 accumulate", 1.0, 8e-2,
+                     "3.8e-2 .. 3.9e-2 (GPU parity tests; 6.3e-2 worst of 2080 baselines at 32 channels)")
 
     # ---- end to end through the host API ----
     # The inputs live in pinned host memory and every step moves them to the
@@ -604,7 +616,7 @@ def main():
                            "chunk_blocks": cb, "x_partials": kz,
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "e2e_copy": e2e_copy,
+                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
                 "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)
     if ws > 1:

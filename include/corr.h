@@ -70,9 +70,12 @@ enum {
   CORR_ETOOBIG = -8   /* corr_correlate_static: the shape needs more than its fixed scratch */
 };
 
-/* Arithmetic of the X step: FP32 on CUDA cores, or FP16 spectra multiplied on
- * the tensor cores with FP32 accumulation (at most 64 stations). */
-enum { CORR_PREC_FP32 = 0, CORR_PREC_FP16_TC = 1 };
+/* Arithmetic of the X step: FP32 on CUDA cores, or FP16 or FP8 (E4M3)
+ * spectra multiplied on the tensor cores with FP32 accumulation (at most 64
+ * stations).  The paper's FX correlator (Abstract: Fourier transform, then
+ * cross-multiply) fixes no arithmetic precision; the reduced-precision modes
+ * trade a stated error against the FP64 definition for tensor-core speed. */
+enum { CORR_PREC_FP32 = 0, CORR_PREC_FP16_TC = 1, CORR_PREC_FP8_TC = 2 };
 
 /* Create a correlator for one scan.  stations 1..256, subbands*pols 1..32,
  * pols 1 or 2, nchan a power of two in 4..8192, tint_s > 0.  *h receives the
@@ -88,11 +91,15 @@ int corr_set_format(corr_t *h, double fs_hz, const float lut[4]);
  * exp(+2 pi i frac(nu0 tau)).  Default 0 (no fringe rotation). */
 int corr_set_sky_freq(corr_t *h, int subband, double nu0_hz);
 
-/* Arithmetic of the X step: CORR_PREC_FP32 (default) or CORR_PREC_FP16_TC.
- * In FP16_TC mode the F step stores X * 2^-floor(log2(N)/2) in FP16 (exact
- * power of two, undone at the end) and the X step runs as a real product of
- * interleaved [Re; Im] station rows on the tensor cores, accumulating in FP32.
- * Only before the first correlate call. */
+/* Arithmetic of the X step: CORR_PREC_FP32 (default), CORR_PREC_FP16_TC or
+ * CORR_PREC_FP8_TC.  In FP16_TC mode the F step stores X * 2^-floor(log2(N)/2)
+ * in FP16 (exact power of two, undone at the end) and the X step runs as a
+ * real product of interleaved [Re; Im] station rows on the tensor cores,
+ * accumulating in FP32.  FP8_TC does the same with E4M3 values (3 mantissa
+ * bits, largest 448) of X * 2^(2 - floor(log2(N)/2)): for 2-bit noise the RMS
+ * of a component sits near 8, values beyond 448 saturate.  Rejects more than
+ * 64 stations for the tensor-core modes (CORR_EINVAL).  Only before the first
+ * correlate call (CORR_ESTATE). */
 int corr_set_precision(corr_t *h, int mode);
 
 /* FFT blocks per F/X chunk (0, the default: as many as fit 1 GiB of FP32

@@ -27,6 +27,7 @@ CORR_EEND = -7
 CORR_ETOOBIG = -8
 CORR_PREC_FP32 = 0
 CORR_PREC_FP16_TC = 1
+CORR_PREC_FP8_TC = 2
 
 _ERRNAMES = {0: "CORR_OK", -1: "CORR_EINVAL", -2: "CORR_ENOMEM", -3: "CORR_EAGAIN", -4: "CORR_ETIMEOUT",
              -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND", -8: "CORR_ETOOBIG"}

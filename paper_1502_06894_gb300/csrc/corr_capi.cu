@@ -98,7 +98,7 @@ struct corr_s {
   size_t spec_budget = (size_t)1 << 30;
   int chunk_req = 0;  // blocks per F/X chunk requested by the caller (0: from spec_budget)
   int sm_count = 0;
-  int sigma = 0;      // FP16 spectra carry X * 2^-sigma
+  int sigma = 0;      // FP16 / FP8 spectra carry X * 2^-sigma
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned
   unsigned char* d_tiles = nullptr;  // tensor-core operand tiles (FFT length <= 2048)
@@ -278,7 +278,9 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   const size_t nbl = (size_t)nbl_of(S);
   w.Mcap = (int)((w.spi + h->N - 1) / h->N) + 1;
   const size_t per_block = (size_t)G * S * nch * sizeof(float2);
-  const bool tc = h->precision == CORR_PREC_FP16_TC;
+  const bool tc = h->precision != CORR_PREC_FP32;
+  const bool fp8 = h->precision == CORR_PREC_FP8_TC;
+  const int kb = fp8 ? 128 : 64;  // blocks per K tile
   int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
   if (h->chunk_req <= 0) {
     // Every chunk reads and writes all partial visibilities once; chunks of at
@@ -292,19 +294,22 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   }
   if (cb < 1) cb = 1;
   if (cb > w.Mcap) cb = w.Mcap;
+  // the tensor cores read whole K tiles: a default chunk of whole tiles leaves
+  // no zero padding except in the last chunk of an integration
+  if (tc && h->chunk_req <= 0 && cb > kb) cb -= cb % kb;
   w.CB = (int)cb;
   w.KZ = xstage_kz(w.CB, S, G, nch);
   // tensor-core operand tiles hold up to 64 stations; for FFTs of up to 2048
-  // points the F step writes them directly, above that FP16 spectra are
+  // points the F step writes them directly, above that FP16 (FP8) spectra are
   // corner-turned into them
   w.tiles = tc && xtc_cpt(S) > 0;
   w.direct = w.tiles && fstage_tc_tiles_supported(nch);
-  w.spec = w.direct ? 16 : (w.tiles ? per_block / 2 * w.CB : per_block * w.CB);
+  w.spec = w.direct ? 16 : (w.tiles ? per_block / (fp8 ? 4 : 2) * w.CB : per_block * w.CB);
   // partial sums: KZ slices for the FP32 X step, one for the tensor cores
   w.part = sizeof(float2) * (size_t)(tc ? 1 : w.KZ) * nbl * G * nch;
   if (w.tiles) {
     const int W = 2 * xtc_cpt(S);
-    w.tiles_bytes = (size_t)G * ((nch + W - 1) / W) * ((size_t)(w.CB + 63) / 64) * 32768;
+    w.tiles_bytes = (size_t)G * ((nch + W - 1) / W) * ((size_t)(w.CB + kb - 1) / kb) * 32768;
   }
   const size_t M = (size_t)w.Mcap;
   w.small = sizeof(StationView) * S + sizeof(int) * S + sizeof(double) * S * kMaxSegs * 7 +
@@ -332,9 +337,12 @@ static int prepare(corr_t* h) {
   h->CB = w.CB;
   h->KZ = w.KZ;
   {
+    // FP16: 2^-floor(log2(N)/2) keeps |X| <= 3.336 N far inside the FP16
+    // range; FP8 (E4M3, largest value 448): four times larger, which puts the
+    // RMS of a component of X (about 1.47 sqrt(N) for 2-bit noise) near 8
     int lg = 0;
     while ((1 << (lg + 1)) <= h->N) ++lg;
-    h->sigma = lg / 2;
+    h->sigma = lg / 2 - (h->precision == CORR_PREC_FP8_TC ? 2 : 0);
   }
   CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->dev), "SM count");
   if ((rc = dalloc(h, (void**)&h->d_views, sizeof(StationView) * S, "views"))) return rc;
@@ -478,15 +486,16 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
   cudaEvent_t pa = nullptr;
   // F and X per chunk
   const int nbl = nbl_of(S);
-  const int kz_used = h->precision == CORR_PREC_FP16_TC ? 1 : h->KZ;
+  const bool tc = h->precision != CORR_PREC_FP32;
+  const bool fp8 = h->precision == CORR_PREC_FP8_TC;
+  const int kz_used = tc ? 1 : h->KZ;
   CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, st),
      "partials memset");
-  const bool tc = h->precision == CORR_PREC_FP16_TC;
   for (int c0 = 0; c0 < M; c0 += h->CB) {
     const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
     FParams fp = fparams(h, c0, cb);
     if (tc) {
-      fp.out_kind = 1;
+      fp.out_kind = fp8 ? 2 : 1;
       fp.scale = ldexpf(1.0f, -h->sigma);
     }
     if (h->tc_tiles) {
@@ -497,15 +506,20 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
       o.cpt = xtc_cpt(S);
       o.W = 2 * o.cpt;
       o.nslice = (h->nchan + o.W - 1) / o.W;
-      o.NKT = (cb + 63) / 64;
+      o.fp8 = fp8 ? 1 : 0;
+      o.NKT = fp8 ? (cb + 127) / 128 : (cb + 63) / 64;
       o.scale = ldexpf(1.0f, -h->sigma);
       pa = prof_begin(h);
       if (h->tc_direct) {
         CK(launch_fstage_tc(fp, o, st), "tensor-core fstage launch");
       } else {
         CK(launch_fstage(fp, st), "fstage launch");
-        CK(launch_tiles(reinterpret_cast<const __half2*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
-           "tile corner-turn launch");
+        if (fp8)
+          CK(launch_tiles8(reinterpret_cast<const uint16_t*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
+             "FP8 tile corner-turn launch");
+        else
+          CK(launch_tiles(reinterpret_cast<const __half2*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
+             "tile corner-turn launch");
       }
       prof_end(h, 1, pa);
       XTC2Params xp;
@@ -517,6 +531,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
       xp.nchan = h->nchan;
       xp.cpt = o.cpt;
       xp.W = o.W;
+      xp.fp8 = o.fp8;
       xp.part = h->d_part;
       xp.err = h->d_err;
       pa = prof_begin(h);
@@ -718,9 +733,9 @@ int corr_set_sky_freq(corr_t* h, int subband, double nu0_hz) {
 
 int corr_set_precision(corr_t* h, int mode) {
   if (!h) return CORR_EINVAL;
-  if (mode != CORR_PREC_FP32 && mode != CORR_PREC_FP16_TC)
+  if (mode != CORR_PREC_FP32 && mode != CORR_PREC_FP16_TC && mode != CORR_PREC_FP8_TC)
     return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
-  if (mode == CORR_PREC_FP16_TC && h->S > 64)
+  if (mode != CORR_PREC_FP32 && h->S > 64)
     return h->fail(CORR_EINVAL, "corr_set_precision: the tensor-core X step takes at most 64 stations");
   if (h->prepared && mode != h->precision)
     return h->fail(CORR_ESTATE, "corr_set_precision: only before the first correlate");

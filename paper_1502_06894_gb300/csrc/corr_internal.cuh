@@ -58,24 +58,28 @@ struct FParams {
   int S, G, npol, nsub, nchan;
   float lut0, lut1, lut2, lut3;
   const float2* twN;        // W_N^m, m < N
-  int out_kind;             // 0: complex FP32 spectra; 1: complex FP16 spectra times `scale`
-  float scale;              // exact power of two (FP16 output only)
+  int out_kind;             // 0: complex FP32 spectra; 1: complex FP16 spectra times `scale`;
+                            // 2: complex E4M3 spectra times `scale` (Re byte, Im byte)
+  float scale;              // exact power of two (FP16 / FP8 output only)
   void* out;                // [G][CB][S][nchan]
 };
 
 // MMA operand tiles written by the tensor-core F step: for stream j, channel
-// slice sl (W channels), K range kt (64 blocks) two 16 KB tiles (channel
-// groups of cpt), tile index ((j * nslice + sl) * NKT + kt) * 2 + group.
+// slice sl (W channels), K range kt (64 blocks of FP16, or 128 blocks of FP8)
+// two 16 KB tiles (channel groups of cpt), tile index
+// ((j * nslice + sl) * NKT + kt) * 2 + group.
 struct TcTiles {
   unsigned char* tiles;
   int nslice, NKT, W, cpt;
-  float scale;              // exact power of two applied before the FP16 rounding
+  int fp8;                  // 0: FP16 tiles (64-block K range); 1: E4M3 tiles (128-block K range)
+  float scale;              // exact power of two applied before the FP16 / FP8 rounding
 };
 
 // X step on tensor cores from operand tiles (see TcTiles).
 struct XTC2Params {
   const unsigned char* tiles;
   int nslice, NKT, S, G, nchan, cpt, W;
+  int fp8;                  // tiles hold E4M3 values (MMA kind::f8f6f4) instead of FP16 (kind::f16)
   float2* part;             // [G][nchan][nbl]
   int* err;
 };
@@ -117,6 +121,9 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s);
 // FP16 spectra [G][CB][S][nchan] (blocks < cb present) -> operand tiles
 cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
                          cudaStream_t s);
+// E4M3 spectra [G][CB][S][nchan] (two bytes: Re, Im) -> FP8 operand tiles
+cudaError_t launch_tiles8(const uint16_t* spec8, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
+                          cudaStream_t s);
 // finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale
 cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s);
 

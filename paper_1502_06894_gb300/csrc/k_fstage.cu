@@ -24,9 +24,16 @@
 // delay segment yet) store zeros, so they add nothing in the X step.
 #include "corr_internal.cuh"
 
+#include <cuda_fp8.h>
 #include <math.h>
 
 namespace corr {
+
+// Complex value -> two E4M3 bytes (Re in the low byte), round to nearest,
+// saturating at +-448.
+__device__ __forceinline__ uint32_t fp8x2(float re, float im) {
+  return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(re, im), __NV_SATFINITE, __NV_E4M3);
+}
 
 __constant__ float2 c_w32[32];  // exp(-2 pi i m / 32)
 
@@ -50,7 +57,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+// Shared FFT buffers insert one padding element after every P elements (P =
+// the first pass's radix): pass 0 stores each thread's P outputs contiguously,
+// so without padding the threads of a half-warp would hit the same banks.
+template <int P>
+__device__ __forceinline__ int padp(int i) { return i + (i >> ilog2c(P)); }
 
 // In-register DFT of R points (R <= 32): radix-2 decimation in frequency,
 // natural-order input, output permuted back to natural order.
@@ -84,9 +95,18 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   for (int r = 0; r < R; ++r) v[r] = t[r];
 }
 
+// Barrier of one FFT group of T threads (groups are T consecutive threads).
+// Groups skip their transform independently (a block that is not valid), so
+// a group never waits for lanes outside it: groups smaller than a warp sync
+// on their own lane mask, larger ones on a named barrier of their own.
 template <int T>
 __device__ __forceinline__ void gsync(int grp) {
-  if constexpr (T <= 32) {
+  if constexpr (T == 1) {
+    // one thread: program order suffices
+  } else if constexpr (T < 32) {
+    const unsigned lane = threadIdx.x & 31u;
+    __syncwarp(((1u << T) - 1u) << (lane & ~(unsigned)(T - 1)));
+  } else if constexpr (T == 32) {
     __syncwarp();
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(T) : "memory");
@@ -95,7 +115,7 @@ __device__ __forceinline__ void gsync(int grp) {
 
 // A later Stockham pass: read R points per butterfly group, twiddle, DFT,
 // write back in place (all reads of the group finish before any write).
-template <int L, int R, int NS, int T>
+template <int L, int R, int NS, int T, int P>
 __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, int grp,
                                               const float2* __restrict__ twN,
                                               const float2* __restrict__ s_twl = nullptr) {
@@ -107,7 +127,7 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
   for (int u = 0; u < PER; ++u) {
     const int j = t + u * T;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[u][r] = buf[pad32(j + r * GROUPS)];
+    for (int r = 0; r < R; ++r) v[u][r] = buf[padp<P>(j + r * GROUPS)];
   }
   gsync<T>(grp);
 #pragma unroll
@@ -124,7 +144,7 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
     dft_reg<R>(v[u]);
     const int idxD = (j / NS) * NS * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[pad32(idxD + r * NS)] = v[u][r];
+    for (int r = 0; r < R; ++r) buf[padp<P>(idxD + r * NS)] = v[u][r];
   }
   gsync<T>(grp);
 }
@@ -149,7 +169,13 @@ template <int L> struct Groups {
   static constexpr int NGRP = T == 1 ? 64 : (T >= 128 ? (256 / T) : 256 / T);
 };
 
-constexpr int kBufPad(int L) { return L + L / 32 + 1; }
+// The tensor-core F step runs 8 groups per stream round (one per block of
+// its 8), or a multiple of 8 when the groups are small.
+template <int L> struct GroupsTC {
+  static constexpr int NGRP = Groups<L>::NGRP >= 8 ? Groups<L>::NGRP : 8;
+};
+
+template <int L> constexpr int kBufPad() { return L + L / Plan<L>::R0 + 1; }
 
 // Shared tables for N <= 2048: the last Stockham pass's twiddles W_L^{k r}
 // (L entries, [r][k]) and the real-split twiddles W_N^k for k <= L/2.
@@ -182,10 +208,109 @@ template <int L> struct LastRadix {
   static constexpr int v = Plan<L>::R2 > 1 ? Plan<L>::R2 : (Plan<L>::R1 > 1 ? Plan<L>::R1 : Plan<L>::R0);
 };
 
+// ---- real split and rotation ----
+// Channels k and L-k come from the same pair Z[k], Z[L-k] of the N/2-point
+// transform:  X[k] = E + W O,  X[L-k] = conj(E - W O),  W = W_N^k.  Z is the
+// transform of the halved samples, so E = Z[k] + conj Z[L-k] and
+// O = -i (Z[k] - conj Z[L-k]) carry the split's factor 1/2.
+template <int L, int R0>
+__device__ __forceinline__ void split_pair(const float2* __restrict__ fbuf, const float2* __restrict__ s_tw,
+                                           const float2* __restrict__ twN, int k, int km, float2& Xa, float2& Xb) {
+  const float2 Zk = fbuf[padp<R0>(k)];
+  const float2 Zm = fbuf[padp<R0>(km)];
+  const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
+  const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
+  const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&twN[k]);
+  const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
+  Xa = make_float2(E.x + WO.x, E.y + WO.y);
+  Xb = make_float2(E.x - WO.x, WO.y - E.y);
+}
+
+// The rotation exp(+2 pi i (phi + k delta)) along a thread's channels
+// k = t + qT (and L - k): the first factor of each sequence comes from the
+// fast sine/cosine of the argument reduced to [-pi, pi] (abs. error ~4e-7),
+// later ones by a walk z <- z + z (e^{i theta} - 1), theta = +-2 pi T delta.
+// |delta| <= 1/(2N) turns per channel (the fractional delay is at most half
+// a sample), so |theta| <= pi T / N <= 0.2 and e^{i theta} - 1 comes from its
+// Taylor series to theta^8 (remainder < 1e-12); written as an increment the
+// walk has no systematic drift of |z| from rounding cos(theta).
+__device__ __forceinline__ float2 cis_turns(float ph) {
+  ph -= rintf(ph);
+  float sn, cs;
+  __sincosf(6.28318530717958648f * ph, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+__device__ __forceinline__ void walk_step(float T_delta, float& cm1, float& sn) {
+  const float th = 6.28318530717958648f * T_delta;
+  const float t2 = th * th;
+  // sin th = th (1 - th^2/3! + th^4/5! - th^6/7!)
+  sn = th * fmaf(t2, fmaf(t2, fmaf(t2, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 1.0f);
+  // cos th - 1 = th^2 (-1/2! + th^2/4! - th^4/6! + th^6/8!)
+  cm1 = t2 * fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f);
+}
+
+__device__ __forceinline__ float2 walk(float2 z, float cm1, float sn) {
+  return make_float2(fmaf(-z.y, sn, fmaf(z.x, cm1, z.x)), fmaf(z.x, sn, fmaf(z.y, cm1, z.y)));
+}
+
+template <int OUT>
+__device__ __forceinline__ void store_spec(void* out, size_t idx, float2 X, float scale) {
+  if constexpr (OUT == 0) {
+    reinterpret_cast<float2*>(out)[idx] = X;
+  } else if constexpr (OUT == 1) {
+    reinterpret_cast<__half2*>(out)[idx] = __floats2half2_rn(X.x * scale, X.y * scale);
+  } else {
+    reinterpret_cast<uint16_t*>(out)[idx] = (uint16_t)fp8x2(X.x * scale, X.y * scale);
+  }
+}
+
+// Split, rotate and store the L/2 + 1 channel pairs of one transform; a
+// block that is not valid stores zeros.
+template <int L, int T, int R0, int OUT>
+__device__ __forceinline__ void split_rotate_store(const float2* __restrict__ fbuf, const float2* __restrict__ s_tw,
+                                                   const float2* __restrict__ twN, int t, bool ok, float phi,
+                                                   float delta, void* out, size_t obase, float scale) {
+  constexpr int HALF = L / 2;
+  constexpr int QF = HALF / T;  // k = t + qT < HALF for q < QF; k = HALF is thread 0's extra
+  const float2 zero = make_float2(0.f, 0.f);
+  if (!ok) {
+#pragma unroll 4
+    for (int q = 0; q < QF; ++q) {
+      const int k = t + q * T;
+      store_spec<OUT>(out, obase + k, zero, scale);
+      if (k != 0) store_spec<OUT>(out, obase + (L - k), zero, scale);
+    }
+    if (t == 0) store_spec<OUT>(out, obase + HALF, zero, scale);
+    return;
+  }
+  float2 z = cis_turns(fmaf((float)t, delta, phi));
+  float2 y = cis_turns(fmaf((float)(L - t), delta, phi));
+  float cm1, sn;
+  walk_step((float)T * delta, cm1, sn);
+#pragma unroll 4
+  for (int q = 0; q < QF; ++q) {
+    const int k = t + q * T;
+    const int km = (L - k) & (L - 1);
+    float2 Xa, Xb;
+    split_pair<L, R0>(fbuf, s_tw, twN, k, km, Xa, Xb);
+    store_spec<OUT>(out, obase + k, cmul(Xa, z), scale);
+    if (k != 0) store_spec<OUT>(out, obase + km, cmul(Xb, y), scale);
+    z = walk(z, cm1, sn);
+    y = walk(y, cm1, -sn);
+  }
+  if (t == 0) {  // k = HALF: X[HALF] = E + W_N^{N/4} O; z has walked to it
+    float2 Xa, Xb;
+    split_pair<L, R0>(fbuf, s_tw, twN, HALF, HALF, Xa, Xb);
+    store_spec<OUT>(out, obase + HALF, cmul(Xa, z), scale);
+  }
+}
+
 // Byte offset of the packed-word staging area after the NGRP FFT buffers,
 // rounded up to 16 bytes for the 16-byte shared-memory stores.
-constexpr size_t kWordsOffset(int L, int NGRP) {
-  return ((size_t)NGRP * kBufPad(L) * sizeof(float2) + 15) & ~(size_t)15;
+template <int L>
+constexpr size_t kWordsOffset(int NGRP) {
+  return ((size_t)NGRP * kBufPad<L>() * sizeof(float2) + 15) & ~(size_t)15;
 }
 
 __host__ __device__ inline int wslot_words(int N, int G) {
@@ -230,6 +355,10 @@ __device__ __forceinline__ void load_pair(const uint32_t* __restrict__ wsl, int 
 template <int L> struct MinBlocks {
   static constexpr int v = (L >= 512 && L <= 1024) ? 2 : (L == 2048 ? 3 : (L == 4096 ? 2 : 1));
 };
+// the tensor-core F step keeps its 8 groups' spectra in shared memory
+template <int L> struct MinBlocksTC {
+  static constexpr int v = Groups<L>::T * GroupsTC<L>::NGRP > 256 ? 1 : MinBlocks<L>::v;
+};
 
 template <int L, int GC>
 __global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)
@@ -238,15 +367,15 @@ k_fstage(FParams p, int slots, int wslot) {
   constexpr int T = P::T;
   constexpr int NGRP = Groups<L>::NGRP;
   constexpr int N = 2 * L;
-  constexpr int BUF = kBufPad(L);
+  constexpr int BUF = kBufPad<L>();
   constexpr int R0 = P::R0;
   constexpr int PER0 = L / R0 / T;
   static_assert(PER0 >= 1, "plan");
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
-  static_assert(kWordsOffset(L, NGRP) % 16 == 0, "staging area must be 16-byte aligned");
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + kWordsOffset(L, NGRP));
+  static_assert(kWordsOffset<L>(NGRP) % 16 == 0, "staging area must be 16-byte aligned");
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem_raw + kWordsOffset<L>(NGRP));
 
   const int tid = threadIdx.x;
   const int grp = tid / T;
@@ -317,8 +446,9 @@ k_fstage(FParams p, int slots, int wslot) {
     const uint32_t* wsl = wbuf + sl * wslot + (GC ? (boff >> 5) : 0);
     const bool even = ((boff >> 5) & 1) == 0;
 
-    // ---- pass 0: unpack straight into registers (NS = 1, no twiddles) ----
-    {
+    // ---- pass 0: unpack straight into registers (NS = 1, no twiddles);
+    //      the transform of a block that is not valid is skipped ----
+    if (ok) {
       float2 v[PER0][R0];
 #pragma unroll
       for (int u = 0; u < PER0; ++u) {
@@ -326,13 +456,9 @@ k_fstage(FParams p, int slots, int wslot) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int m = jj + r * (L / R0);
-          float2 xv = make_float2(0.f, 0.f);
-          if (ok) {
-            uint32_t c0, c1;
-            load_pair<GC>(wsl, boff, G, m, j, even, c0, c1);
-            xv = s_lut16[c0 | (c1 << 2)];
-          }
-          v[u][r] = xv;
+          uint32_t c0, c1;
+          load_pair<GC>(wsl, boff, G, m, j, even, c0, c1);
+          v[u][r] = s_lut16[c0 | (c1 << 2)];
         }
       }
 #pragma unroll
@@ -340,63 +466,27 @@ k_fstage(FParams p, int slots, int wslot) {
         const int jj = t + u * T;
         dft_reg<R0>(v[u]);
 #pragma unroll
-        for (int r = 0; r < R0; ++r) fbuf[pad32(jj * R0 + r)] = v[u][r];
+        for (int r = 0; r < R0; ++r) fbuf[padp<R0>(jj * R0 + r)] = v[u][r];
       }
       gsync<T>(grp);
+      if constexpr (P::R1 > 1)
+        stockham_pass<L, P::R1, P::R0, T, P::R0>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
+      if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0>(fbuf, t, grp, p.twN);
     }
-    if constexpr (P::R1 > 1)
-      stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
-    if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
 
     // ---- real split, rotation, store ----
-    // channels k and L-k come from the same pair Z[k], Z[L-k]:
-    //   X[k] = E + W O,  X[L-k] = conj(E - W O),  W = W_N^k
     if (active) {
       const int d = p.blk0 + bb0 + sl;
       const int bb = bb0 + sl;
-      const float delta = p.delta[(size_t)s * p.ld + d];
-      const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
-      float2* out = reinterpret_cast<float2*>(p.out) + (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
-      constexpr int HALF = L / 2;
-      constexpr int QN = HALF / T + 1;  // k runs over 0..HALF
-#pragma unroll 4
-      for (int q = 0; q < QN; ++q) {
-        const int k = t + q * T;
-        if (k > HALF) break;
-        float2 Xa = make_float2(0.f, 0.f), Xb = make_float2(0.f, 0.f);
-        const int km = (L - k) & (L - 1);
-        if (ok) {
-          // Z is the transform of the halved samples, so E = Z[k] + conj Z[L-k]
-          // and O = -i (Z[k] - conj Z[L-k]) carry the split's factor 1/2
-          const float2 Zk = fbuf[pad32(k)];
-          const float2 Zm = fbuf[pad32(km)];
-          const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
-          const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
-          const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&p.twN[k]);
-          const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
-          Xa = make_float2(E.x + WO.x, E.y + WO.y);
-          Xb = make_float2(E.x - WO.x, WO.y - E.y);
-          // rotation exp(+2 pi i (phi + k delta)); the argument is reduced to
-          // [-pi, pi] first, where the fast sine/cosine is accurate to ~4e-7
-          float ph = fmaf((float)k, delta, phi);
-          ph -= rintf(ph);
-          float sn, cs;
-          __sincosf(6.28318530717958648f * ph, &sn, &cs);
-          Xa = make_float2(Xa.x * cs - Xa.y * sn, Xa.x * sn + Xa.y * cs);
-          float ph2 = fmaf((float)km, delta, phi);
-          ph2 -= rintf(ph2);
-          __sincosf(6.28318530717958648f * ph2, &sn, &cs);
-          Xb = make_float2(Xb.x * cs - Xb.y * sn, Xb.x * sn + Xb.y * cs);
-        }
-        if (p.out_kind == 1) {
-          __half2* o16 = reinterpret_cast<__half2*>(p.out) + (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
-          o16[k] = __floats2half2_rn(Xa.x * p.scale, Xa.y * p.scale);
-          if (k != 0 && k != HALF) o16[km] = __floats2half2_rn(Xb.x * p.scale, Xb.y * p.scale);
-        } else {
-          out[k] = Xa;
-          if (k != 0 && k != HALF) out[km] = Xb;
-        }
-      }
+      const float delta = ok ? p.delta[(size_t)s * p.ld + d] : 0.f;
+      const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
+      const size_t obase = (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
+      if (p.out_kind == 1)
+        split_rotate_store<L, T, R0, 1>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
+      else if (p.out_kind == 2)
+        split_rotate_store<L, T, R0, 2>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
+      else
+        split_rotate_store<L, T, R0, 0>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
     }
     gsync<T>(grp);
   }
@@ -416,6 +506,10 @@ k_fstage(FParams p, int slots, int wslot) {
 // FP16 spectra in shared memory, then all threads corner-turn them: for each
 // channel and Re/Im the 8 blocks become one 16-byte store.  The packed
 // samples are read straight from global memory (L1-cached across streams).
+//
+// FP8 (E4M3) tiles have the same geometry with one byte per value: a tile
+// row holds 128 blocks, so a K tile spans 128 blocks and the 8 blocks of a
+// CTA fill one half (8 bytes) of a 16-byte chunk.
 
 template <int GC>
 __device__ __forceinline__ void load_pair_g(const StationView& sv, int64_t rel, int G, int m, int j,
@@ -432,15 +526,15 @@ __device__ __forceinline__ void load_pair_g(const StationView& sv, int64_t rel, 
   }
 }
 
-template <int L, int GC>
-__global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)
+template <int L, int GC, bool FP8>
+__global__ void __launch_bounds__(Groups<L>::T * GroupsTC<L>::NGRP, MinBlocksTC<L>::v)
 k_fstage_tc(FParams p, TcTiles o) {
   using P = Plan<L>;
   constexpr int T = P::T;
-  constexpr int NGRP = Groups<L>::NGRP;
+  constexpr int NGRP = GroupsTC<L>::NGRP;
   static_assert(NGRP >= 8 && NGRP % 8 == 0, "the tile writer needs 8 groups per stream");
   constexpr int SPR = NGRP / 8;  // streams per round
-  constexpr int BUF = kBufPad(L);
+  constexpr int BUF = kBufPad<L>();
   constexpr int R0 = P::R0;
   constexpr int PER0 = L / R0 / T;
   constexpr int HALF = L / 2;
@@ -466,14 +560,17 @@ k_fstage_tc(FParams p, TcTiles o) {
   const bool valid = present && p.valid[(size_t)s * p.ld + d] != 0;
   const int64_t rel = valid ? p.start[(size_t)s * p.ld + d] - sv.sample0 : 0;
   const float delta = valid ? p.delta[(size_t)s * p.ld + d] : 0.f;
-  const int kt = (blockIdx.x * 8) / 64;
-  const int kc = (blockIdx.x & 7);  // 16-byte chunk of the 64-block K range
+  constexpr int KB = FP8 ? 128 : 64;                  // blocks per K tile
+  const int kt = (blockIdx.x * 8) / KB;
+  const int kc = FP8 ? ((blockIdx.x & 15) >> 1) : (blockIdx.x & 7);  // 16-byte chunk of the K range
+  const int khalf = FP8 ? (blockIdx.x & 1) * 8 : 0;   // byte offset of the FP8 half chunk
 
   for (int r0 = 0; r0 < G; r0 += SPR) {
     const int j = r0 + grp / 8;
     const bool ok = valid && j < G;
-    // ---- pass 0 from global memory ----
-    {
+    // ---- pass 0 from global memory (skipped for blocks that are absent or
+    //      not valid: their spectra are zeros) ----
+    if (ok) {
       float2 v[PER0][R0];
 #pragma unroll
       for (int u = 0; u < PER0; ++u) {
@@ -481,13 +578,9 @@ k_fstage_tc(FParams p, TcTiles o) {
 #pragma unroll
         for (int r = 0; r < R0; ++r) {
           const int m = jj + r * (L / R0);
-          float2 xv = make_float2(0.f, 0.f);
-          if (ok) {
-            uint32_t c0, c1;
-            load_pair_g<GC>(sv, rel, G, m, j, c0, c1);
-            xv = s_lut16[c0 | (c1 << 2)];
-          }
-          v[u][r] = xv;
+          uint32_t c0, c1;
+          load_pair_g<GC>(sv, rel, G, m, j, c0, c1);
+          v[u][r] = s_lut16[c0 | (c1 << 2)];
         }
       }
 #pragma unroll
@@ -495,52 +588,66 @@ k_fstage_tc(FParams p, TcTiles o) {
         const int jj = t + u * T;
         dft_reg<R0>(v[u]);
 #pragma unroll
-        for (int r = 0; r < R0; ++r) fbuf[pad32(jj * R0 + r)] = v[u][r];
+        for (int r = 0; r < R0; ++r) fbuf[padp<R0>(jj * R0 + r)] = v[u][r];
       }
       gsync<T>(grp);
+      if constexpr (P::R1 > 1)
+        stockham_pass<L, P::R1, P::R0, T, P::R0>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
+      if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0>(fbuf, t, grp, p.twN);
     }
-    if constexpr (P::R1 > 1)
-      stockham_pass<L, P::R1, P::R0, T>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
-    if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T>(fbuf, t, grp, p.twN);
 
-    // ---- real split + rotation into registers, then FP16 into the group's buffer ----
-    const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
+    // ---- real split + rotation into registers, then FP16 / FP8 into the group's buffer ----
+    constexpr int QF = HALF / T;  // k = t + qT < HALF for q < QF; k = HALF is thread 0's extra
     float2 xa[QN], xb[QN];
 #pragma unroll
     for (int q = 0; q < QN; ++q) {
-      const int k = t + q * T;
       xa[q] = make_float2(0.f, 0.f);
       xb[q] = make_float2(0.f, 0.f);
-      if (ok && k <= HALF) {
-        const int km = (L - k) & (L - 1);
-        const float2 Zk = fbuf[pad32(k)];
-        const float2 Zm = fbuf[pad32(km)];
-        const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
-        const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
-        const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&p.twN[k]);
-        const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
-        float2 Xa = make_float2(E.x + WO.x, E.y + WO.y);
-        float2 Xb = make_float2(E.x - WO.x, WO.y - E.y);
-        float ph = fmaf((float)k, delta, phi);
-        ph -= rintf(ph);
-        float sn, cs;
-        __sincosf(6.28318530717958648f * ph, &sn, &cs);
-        xa[q] = make_float2(Xa.x * cs - Xa.y * sn, Xa.x * sn + Xa.y * cs);
-        float ph2 = fmaf((float)km, delta, phi);
-        ph2 -= rintf(ph2);
-        __sincosf(6.28318530717958648f * ph2, &sn, &cs);
-        xb[q] = make_float2(Xb.x * cs - Xb.y * sn, Xb.x * sn + Xb.y * cs);
+    }
+    if (ok) {
+      const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
+      float2 z = cis_turns(fmaf((float)t, delta, phi));
+      float2 y = cis_turns(fmaf((float)(L - t), delta, phi));
+      float cm1, sn;
+      walk_step((float)T * delta, cm1, sn);
+#pragma unroll
+      for (int q = 0; q < QF; ++q) {
+        const int k = t + q * T;
+        float2 Xa, Xb;
+        split_pair<L, R0>(fbuf, s_tw, p.twN, k, (L - k) & (L - 1), Xa, Xb);
+        xa[q] = cmul(Xa, z);
+        xb[q] = cmul(Xb, y);
+        z = walk(z, cm1, sn);
+        y = walk(y, cm1, -sn);
+      }
+      if (t == 0) {
+        float2 Xa, Xb;
+        split_pair<L, R0>(fbuf, s_tw, p.twN, HALF, HALF, Xa, Xb);
+        xa[QF] = cmul(Xa, z);
       }
     }
     gsync<T>(grp);
-    __half2* xh = reinterpret_cast<__half2*>(fbuf);
+    if constexpr (FP8) {
+      uint16_t* x8 = reinterpret_cast<uint16_t*>(fbuf);
 #pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      const int k = t + q * T;
-      if (k <= HALF) {
-        const int km = (L - k) & (L - 1);
-        xh[k] = __floats2half2_rn(xa[q].x * o.scale, xa[q].y * o.scale);
-        if (k != 0 && k != HALF) xh[km] = __floats2half2_rn(xb[q].x * o.scale, xb[q].y * o.scale);
+      for (int q = 0; q < QN; ++q) {
+        const int k = t + q * T;
+        if (k <= HALF) {
+          const int km = (L - k) & (L - 1);
+          x8[k] = (uint16_t)fp8x2(xa[q].x * o.scale, xa[q].y * o.scale);
+          if (k != 0 && k != HALF) x8[km] = (uint16_t)fp8x2(xb[q].x * o.scale, xb[q].y * o.scale);
+        }
+      }
+    } else {
+      __half2* xh = reinterpret_cast<__half2*>(fbuf);
+#pragma unroll
+      for (int q = 0; q < QN; ++q) {
+        const int k = t + q * T;
+        if (k <= HALF) {
+          const int km = (L - k) & (L - 1);
+          xh[k] = __floats2half2_rn(xa[q].x * o.scale, xa[q].y * o.scale);
+          if (k != 0 && k != HALF) xh[km] = __floats2half2_rn(xb[q].x * o.scale, xb[q].y * o.scale);
+        }
       }
     }
     __syncthreads();
@@ -551,6 +658,28 @@ k_fstage_tc(FParams p, TcTiles o) {
       const int k = it - ss * L;
       const int jo = r0 + ss;
       if (jo >= G) continue;
+      const int sl = k / o.W;
+      const int cw = k - sl * o.W;
+      const int tg = cw / o.cpt;
+      const int cl = cw - tg * o.cpt;
+      const int r = (cl * p.S + s) * 2;
+      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+      if constexpr (FP8) {
+        // 8 blocks x (Re byte, Im byte) -> 8 Re bytes and 8 Im bytes
+        uint32_t w[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) w[e] = reinterpret_cast<const uint16_t*>(fbuf_all + (ss * 8 + e) * BUF)[k];
+        const uint32_t r01 = __byte_perm(w[0], w[1], 0x0040), r23 = __byte_perm(w[2], w[3], 0x0040);
+        const uint32_t r45 = __byte_perm(w[4], w[5], 0x0040), r67 = __byte_perm(w[6], w[7], 0x0040);
+        const uint32_t i01 = __byte_perm(w[0], w[1], 0x0051), i23 = __byte_perm(w[2], w[3], 0x0051);
+        const uint32_t i45 = __byte_perm(w[4], w[5], 0x0051), i67 = __byte_perm(w[6], w[7], 0x0051);
+        *reinterpret_cast<uint2*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4) + khalf) =
+            make_uint2(__byte_perm(r01, r23, 0x5410), __byte_perm(r45, r67, 0x5410));
+        const int r1 = r + 1;
+        *reinterpret_cast<uint2*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4) + khalf) =
+            make_uint2(__byte_perm(i01, i23, 0x5410), __byte_perm(i45, i67, 0x5410));
+        continue;
+      }
       uint32_t re[4], im[4];
 #pragma unroll
       for (int e = 0; e < 8; e += 2) {
@@ -559,12 +688,6 @@ k_fstage_tc(FParams p, TcTiles o) {
         re[e / 2] = (uint32_t)__half_as_ushort(__low2half(a)) | ((uint32_t)__half_as_ushort(__low2half(b)) << 16);
         im[e / 2] = (uint32_t)__half_as_ushort(__high2half(a)) | ((uint32_t)__half_as_ushort(__high2half(b)) << 16);
       }
-      const int sl = k / o.W;
-      const int cw = k - sl * o.W;
-      const int tg = cw / o.cpt;
-      const int cl = cw - tg * o.cpt;
-      const int r = (cl * p.S + s) * 2;
-      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
       *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
           make_uint4(re[0], re[1], re[2], re[3]);
       const int r1 = r + 1;
@@ -575,23 +698,29 @@ k_fstage_tc(FParams p, TcTiles o) {
   }
 }
 
-template <int L, int GC>
+template <int L, int GC, bool FP8>
 static cudaError_t launch_tc_LG(const FParams& p, const TcTiles& o, cudaStream_t st) {
   constexpr int T = Plan<L>::T;
-  constexpr int NGRP = Groups<L>::NGRP;
-  const size_t smem = (size_t)NGRP * kBufPad(L) * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_fstage_tc<L, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int NGRP = GroupsTC<L>::NGRP;
+  const size_t smem = (size_t)NGRP * kBufPad<L>() * sizeof(float2);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_fstage_tc<L, GC, FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(o.NKT * 8, p.S);
-  k_fstage_tc<L, GC><<<grid, T * NGRP, smem, st>>>(p, o);
+  // whole K tiles: blocks at or beyond CB are written as zeros
+  dim3 grid(o.NKT * (FP8 ? 16 : 8), p.S);
+  k_fstage_tc<L, GC, FP8><<<grid, T * NGRP, smem, st>>>(p, o);
   return cudaGetLastError();
 }
 
 template <int L>
 static cudaError_t launch_tc_L(const FParams& p, const TcTiles& o, cudaStream_t st) {
-  if constexpr (Groups<L>::NGRP >= 8 && Groups<L>::NGRP % 8 == 0) {
-    if (p.G == 16) return launch_tc_LG<L, 16>(p, o, st);
-    return launch_tc_LG<L, 0>(p, o, st);
+  if constexpr (GroupsTC<L>::NGRP % 8 == 0 && Plan<L>::T * GroupsTC<L>::NGRP <= 1024) {
+    if (o.fp8) {
+      if (p.G == 16) return launch_tc_LG<L, 16, true>(p, o, st);
+      return launch_tc_LG<L, 0, true>(p, o, st);
+    }
+    if (p.G == 16) return launch_tc_LG<L, 16, false>(p, o, st);
+    return launch_tc_LG<L, 0, false>(p, o, st);
   } else {
     return cudaErrorInvalidValue;
   }
@@ -624,7 +753,7 @@ static cudaError_t launch_LG(const FParams& p, cudaStream_t st) {
   if (slots < 1) slots = 1;
   if (slots > 64) slots = 64;
   const int wslot = wslot_words(N, p.G);
-  const size_t smem = kWordsOffset(L, NGRP) + (size_t)slots * wslot * sizeof(uint32_t);
+  const size_t smem = kWordsOffset<L>(NGRP) + (size_t)slots * wslot * sizeof(uint32_t);
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_fstage<L, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

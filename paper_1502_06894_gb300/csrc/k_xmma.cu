@@ -1,5 +1,5 @@
 // k_xmma.cu -- the X step on the 5th-generation tensor cores (tcgen05), FP16
-// inputs with FP32 accumulation in tensor memory (TMEM).
+// or FP8 (E4M3) inputs with FP32 accumulation in tensor memory (TMEM).
 //
 // For one stream g and channel k the X step is a Hermitian outer product over
 // the FFT blocks b of an integration:  V_ab = sum_b X_a[b] conj(X_b[b]).  With
@@ -7,15 +7,17 @@
 // product P = R R^T holds every term:
 //     V_ab = (P[2a][2b] + P[2a+1][2b+1]) + i (P[2a+1][2b] - P[2a][2b+1]).
 // Several channels share one 128-row tile (cpt = floor(64/S) channels of 2S
-// rows), so one M=N=128, K=16 MMA (kind::f16) serves them all; the products
-// across different channels are computed and discarded.  A = B = the same
-// shared-memory tile.
+// rows), so one M=N=128 MMA (K=16 of kind::f16, or K=32 of kind::f8f6f4)
+// serves them all; the products across different channels are computed and
+// discarded.  A = B = the same shared-memory tile.
 //
-// Operand tiles: 128 rows x 64 blocks of FP16, K-major with the 128-byte
-// swizzle, written by the F step (directly, or by the corner turn k_tiles
-// from FP16 spectra); the X kernel k_xmma2 streams them with bulk copies into
-// shared memory, issues the MMAs into TMEM accumulators and adds V_ab into
-// FP32 partial sums in global memory.
+// Operand tiles: 128 rows x 128 bytes, K-major with the 128-byte swizzle:
+// 64 blocks of FP16 or 128 blocks of E4M3 per row, written by the F step
+// (directly, or by the corner turns k_tiles / k_tiles8 from FP16 / FP8
+// spectra); the X kernel k_xmma2 streams them with bulk copies into shared
+// memory, issues the MMAs into TMEM accumulators and adds V_ab into FP32
+// partial sums in global memory.  Both element types advance 32 bytes of a
+// row per MMA, so the shared-memory descriptors are the same.
 // Every wait on an mbarrier is bounded; on timeout the CTA sets *err, stops
 // issuing work, waits for its own copies, frees its TMEM and returns.
 #include "corr_internal.cuh"
@@ -42,12 +44,20 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
          (2ull << 61) /* 128-byte swizzle */;
 }
 
-// kind::f16 instruction descriptor: D FP32, A = B = FP16, both K-major, N = M = 128.
+// Instruction descriptor: D FP32 (bits 4-5 = 1), A and B format code 0 (FP16
+// for kind::f16, E4M3 for kind::f8f6f4), both K-major, N = M = 128.
 constexpr uint32_t kIdesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
   asm volatile(
       "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }" ::"r"(
           tmem_d),
       "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
 }
@@ -103,6 +113,7 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, 
 
 }  // namespace
 
+template <bool FP8>
 __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -172,8 +183,13 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
         for (int grp = 0; grp < 2; ++grp) {
           const uint64_t d0 = sw128_desc(smem_u32(ring + st * kPairBytes + grp * kTileBytes));
 #pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            mma_f16(taddr + ab * 256 + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (kt > 0 || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < 4; ++ks) {
+            // 32 bytes of each row per MMA: K = 16 FP16 or K = 32 E4M3 values
+            if constexpr (FP8)
+              mma_f8(taddr + ab * 256 + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (kt > 0 || ks > 0) ? 1u : 0u);
+            else
+              mma_f16(taddr + ab * 256 + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (kt > 0 || ks > 0) ? 1u : 0u);
+          }
         }
         mma_commit(&s_empty[st]);
         if (kt == NKT - 1) mma_commit(&s_acc_full[ab]);
@@ -248,10 +264,16 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
   const int nitems = p.G * p.nslice;
   if (nitems <= 0 || p.NKT <= 0) return cudaSuccess;
   const size_t smem = 1024 + (size_t)kStages2 * kPairBytes;
-  cudaError_t e = cudaFuncSetAttribute(k_xmma2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const int grid = nitems < sm_count ? nitems : sm_count;
-  k_xmma2<<<grid, 160, smem, s>>>(p, nitems);
+  if (p.fp8) {
+    cudaError_t e = cudaFuncSetAttribute(k_xmma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_xmma2<true><<<grid, 160, smem, s>>>(p, nitems);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(k_xmma2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_xmma2<false><<<grid, 160, smem, s>>>(p, nitems);
+  }
   return cudaGetLastError();
 }
 
@@ -266,7 +288,32 @@ cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
 //   write   8 threads per row, one 16-byte chunk each, to the chunk's swizzled
 //           place: every tile row is written as one whole 128-byte line.
 // Blocks at or beyond cb are written as zeros (the MMA reads whole K tiles).
-constexpr int kTurnRow = 144;  // bytes per staged row (64 FP16 + 16 bytes of padding)
+constexpr int kTurnRow = 144;  // bytes per staged row (128 bytes of values + 16 bytes of padding)
+
+// Write phase of both corner turns: 8 threads per staged row, one 16-byte
+// chunk each, to the chunk's swizzled place, so every tile row is written as
+// one whole 128-byte line.
+__device__ __forceinline__ void write_staged_rows(const unsigned char* turn_raw, const TcTiles& o, int S, int nch,
+                                                  int CH, int c0, int kt, int jo) {
+  const int nitems = 2 * S * nch * 8;
+  for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
+    const int kc = i & 7;
+    const int row = i >> 3;  // (ri * S + s) * nch + c
+    const int c = row % nch;
+    const int rs = row / nch;
+    const int s = rs % S;
+    const int ri = rs / S;
+    const uint4 v = *reinterpret_cast<const uint4*>(turn_raw + ((size_t)rs * CH + c) * kTurnRow + kc * 16);
+    const int k = c0 + c;
+    const int sl = k / o.W;
+    const int cw = k - sl * o.W;
+    const int tg = cw / o.cpt;
+    const int cl = cw - tg * o.cpt;
+    const int r = (cl * S + s) * 2 + ri;
+    unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+    *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) = v;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec, TcTiles o, int CB, int cb, int S,
                                                int nchan, int CH) {
@@ -311,24 +358,55 @@ __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec,
     }
   }
   __syncthreads();
-  const int nitems = 2 * S * nch * 8;
-  for (int i = tid; i < nitems; i += blockDim.x) {
-    const int kc = i & 7;
-    const int row = i >> 3;  // (ri * S + s) * nch + c
-    const int c = row % nch;
-    const int rs = row / nch;
-    const int s = rs % S;
-    const int ri = rs / S;
-    const uint4 v = *reinterpret_cast<const uint4*>(turn_raw + ((size_t)rs * CH + c) * kTurnRow + kc * 16);
-    const int k = c0 + c;
-    const int sl = k / o.W;
-    const int cw = k - sl * o.W;
-    const int tg = cw / o.cpt;
-    const int cl = cw - tg * o.cpt;
-    const int r = (cl * S + s) * 2 + ri;
-    unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
-    *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) = v;
+  write_staged_rows(turn_raw, o, S, nch, CH, c0, kt, jo);
+}
+
+// FP8 corner turn: the same, for E4M3 spectra (two bytes per channel: Re,
+// Im) and 128-block K tiles.  A thread takes 8 channels (one 16-byte read) x
+// 4 consecutive blocks of one station and stores per channel 4 Re and 4 Im
+// bytes; threads run over blocks fastest, so a warp fills one whole 128-byte
+// staged row.
+__global__ void __launch_bounds__(256) k_tiles8(const uint16_t* __restrict__ spec8, TcTiles o, int CB, int cb,
+                                                int S, int nchan, int CH) {
+  extern __shared__ __align__(16) unsigned char turn_raw[];  // [Re/Im][S][CH] rows of kTurnRow bytes
+  const int c0 = blockIdx.x * CH;
+  const int kt = blockIdx.y;
+  const int jo = blockIdx.z;
+  const int nch = min(CH, nchan - c0);
+  const int tid = threadIdx.x;
+  const int CV = CH / 8;
+  const int nstage = S * CV * 32;
+  for (int i = tid; i < nstage; i += blockDim.x) {
+    const int b4 = i & 31;
+    const int j = i >> 5;
+    const int c = 8 * (j % CV);
+    const int sb = j / CV;
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int bg = kt * 128 + 4 * b4 + u;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (c < nch && bg < cb)
+        v[u] = __ldg(reinterpret_cast<const uint4*>(spec8 + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = e >> 1;
+        w[u] = q == 0 ? v[u].x : q == 1 ? v[u].y : q == 2 ? v[u].z : v[u].w;
+      }
+      // channel e sits in bytes 0,1 (even e) or 2,3 (odd e) of its word
+      const uint32_t sre = (e & 1) ? 0x0062u : 0x0040u, sim = (e & 1) ? 0x0073u : 0x0051u;
+      const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], sre), __byte_perm(w[2], w[3], sre), 0x5410);
+      const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], sim), __byte_perm(w[2], w[3], sim), 0x5410);
+      *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 4 * b4) = re;
+      *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 4 * b4) = im;
+    }
   }
+  __syncthreads();
+  write_staged_rows(turn_raw, o, S, nch, CH, c0, kt, jo);
 }
 
 cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
@@ -342,6 +420,20 @@ cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, 
   if (e != cudaSuccess) return e;
   dim3 grid((nchan + CH - 1) / CH, o.NKT, G);
   k_tiles<<<grid, 256, smem, s>>>(spec, o, CB, cb, S, nchan, CH);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tiles8(const uint16_t* spec8, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
+                          cudaStream_t s) {
+  if (cb <= 0) return cudaSuccess;
+  if (nchan % 8) return cudaErrorInvalidValue;
+  int CH = 16;
+  while (CH > 8 && (size_t)2 * S * CH * kTurnRow > 110 * 1024) CH /= 2;
+  const size_t smem = (size_t)2 * S * CH * kTurnRow;
+  cudaError_t e = cudaFuncSetAttribute(k_tiles8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nchan + CH - 1) / CH, o.NKT, G);
+  k_tiles8<<<grid, 256, smem, s>>>(spec8, o, CB, cb, S, nchan, CH);
   return cudaGetLastError();
 }
 
