@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--chunk-blocks", type=int, default=0, help="FFT blocks per F/X chunk (0: library default)")
     ap.add_argument("--duration", type=float, default=10.0,
                     help="scan length in seconds (10 s is the benchmark; shorter only for profiling)")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense 64-station X-step leg")
+    ap.add_argument("--dense-duration", type=float, default=0.5,
+                    help="seconds of the 64-station scan in the dense leg (the named scan is 4 s)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-scan batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served leg")
     ap.add_argument("--batch-scans", type=int, default=96)
@@ -240,6 +243,93 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def dense_leg(args, torch, corr, dev):
+    """The X step where the station count makes it dense: 64 stations,
+    16 subbands x 2 pols at 64 Msample/s, 4096 channels (8192-point FFTs),
+    0.25 s integrations, on a --dense-duration slice of the 4 s scan.  Each
+    precision correlates the same device-resident samples; reported per
+    precision: station-samples/s, the X step's algorithmic TFLOP/s
+    (8 flop per baseline, channel and block) and, on the tensor cores, the
+    issued MMA rate (the real [Re; Im] product does about twice the
+    algorithmic work) against the measured dense BF16 peak (x2 for FP8)."""
+    import synth
+    D = args.dense_duration
+    sc = synth.config2(seed=3, duration=D, tint=0.25, boundary=D / 2, nchan=4096, stations=64, nsub=16, npol=2,
+                       fs=64e6, nu0_base=1.6e9)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3003)
+    streams = [device_codes(sc.nsamp[s] * sc.G // 4, gen, dev) for s in range(sc.stations)]
+    torch.cuda.synchronize()
+    nint = int(round(D / sc.tint))
+    spi = int(round(sc.fs * sc.tint))
+    N = 2 * sc.nchan
+    blocks = sum(-(-(i + 1) * spi // N) - (-(-i * spi // N)) for i in range(nint))
+    x_flops = 8.0 * blocks * sc.G * sc.nchan * sc.nbl
+    mma_flops = 2.0 * blocks * sc.G * (sc.nchan // 2) * 2 * 128 * 128  # 2 tiles of 128 rows per 2 channels
+    sps = sc.stations * sc.G * nint * spi
+    out = torch.empty((sc.nbl, sc.G, sc.nchan), dtype=torch.complex64, device=dev)
+    w = torch.empty(sc.nbl, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    bf16 = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        bf16 = 1900.0
+    res = {"workload": "cfg3 slice: 64 stations, 16 subbands x 32 MHz, 2 pols, 2-bit, %.2f s of the 4 s scan, "
+                       "4096 channels, 0.25 s integrations" % D,
+           "station_samples_per_step": sps, "input_bytes": int(sum(int(t.numel()) for t in streams))}
+    for name, prec, bound, measured in (("fp32", corr.CORR_PREC_FP32, 1e-5, "<= 1e-5 (GPU parity tests)"),
+                                        ("fp16", corr.CORR_PREC_FP16_TC, 1.5e-3, "3.1e-4 (64-station parity test)"),
+                                        ("fp8", corr.CORR_PREC_FP8_TC, 8e-2, "3.9e-2 (64-station parity test)")):
+        c = corr.from_scan(sc, device_streams=streams)
+        c.set_precision(prec)
+        c.set_stream(stream.cuda_stream)
+        c.flush()
+
+        def step():
+            c.rewind()
+            for _ in range(nint):
+                rc = c.correlate_device(out, w)
+                if rc != corr.CORR_OK:
+                    raise RuntimeError("correlate_device returned %d" % rc)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        c.read_profile()
+        c.set_profiling(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(k):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        prof = c.read_profile()
+        cb, _ = c.launch_shape()
+        c.close()
+        x_ms = prof["xstage"][0] / k
+        r = {"value": sps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms, "steps": k, "chunk_blocks": cb,
+             "fstage_ms_per_step": prof["fstage"][0] / k, "xstep_ms_per_step": x_ms,
+             "xstep_tflops": x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None,
+             "error_bound_rel_rms": bound, "measured_rel_rms": measured}
+        if prec != corr.CORR_PREC_FP32 and x_ms > 0:
+            peak = bf16 * (2.0 if prec == corr.CORR_PREC_FP8_TC else 1.0)
+            r["xstep_mma_tflops_issued"] = mma_flops / (x_ms / 1e3) / 1e12
+            r["tensor_peak_tflops"] = peak
+            r["tensor_frac"] = r["xstep_mma_tflops_issued"] / peak
+        res[name] = r
+    for name in ("fp16", "fp8"):
+        if res["fp32"]["xstep_ms_per_step"] > 0:
+            res[name]["xstep_vs_fp32_xstep"] = res["fp32"]["xstep_ms_per_step"] / res[name]["xstep_ms_per_step"]
+    del streams
+    torch.cuda.empty_cache()
+    return res
 
 
 def batch_leg(args, torch, corr, dev):
@@ -587,10 +677,13 @@ def main():
 
     batch = None
     served = None
+    dense = None
     if rank == 0 and ws == 1:
         # free the single-scan buffers first: the mix brings its own pool
         del out, wts
         torch.cuda.empty_cache()
+        if not args.no_dense:
+            dense = dense_leg(args, torch, corr, dev)
         if not args.no_batch:
             batch = batch_leg(args, torch, corr, dev)
         if not args.no_serve:
@@ -617,7 +710,7 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
-                "batch": batch, "serve": served}
+                "dense": dense, "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

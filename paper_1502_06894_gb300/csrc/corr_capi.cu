@@ -287,9 +287,20 @@ static int work_layout(corr_t* h, WorkLayout& w) {
     // least 32 (S + 1) / b blocks (b = bytes per complex spectrum value) keep
     // that traffic near a quarter of the spectra the X step reads.  On the
     // tensor cores a chunk of 512 blocks also gives each accumulator 8 K tiles
-    // before its read-out.  Up to four times the spectra budget is spent on it.
+    // before its read-out.  Up to four times the FP32 spectra budget is spent
+    // on it; the tensor cores count what they hold per block (operand tiles,
+    // plus FP16 / FP8 spectra when a corner turn builds the tiles) against
+    // sixteen times the budget, since at many stations every accumulator
+    // read-out costs as much as several K tiles.
     const int64_t want = tc ? std::max<int64_t>(8 * (int64_t)(S + 1), 512) : 4 * (int64_t)(S + 1);
-    const int64_t cap = (int64_t)(4 * h->spec_budget / per_block);
+    int64_t cap = (int64_t)(4 * h->spec_budget / per_block);
+    if (tc && xtc_cpt(S) > 0) {
+      const int W = 2 * xtc_cpt(S);
+      const size_t tiles_per_block = (size_t)G * ((nch + W - 1) / W) * 32768 / kb;
+      const size_t tc_per_block =
+          tiles_per_block + (fstage_tc_tiles_supported(nch) ? 0 : per_block / (fp8 ? 4 : 2));
+      cap = std::max<int64_t>(cap, (int64_t)(16 * h->spec_budget / tc_per_block));
+    }
     if (cb < want) cb = std::min(want, std::max(cap, cb));
   }
   if (cb < 1) cb = 1;

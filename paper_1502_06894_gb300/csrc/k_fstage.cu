@@ -314,28 +314,23 @@ constexpr size_t kWordsOffset(int NGRP) {
 }
 
 __host__ __device__ inline int wslot_words(int N, int G) {
-  // window bits 2*N*G plus up to 31 bits of misalignment, plus one spare word
-  return (((2 * N * G + 31 + 31) >> 5) + 1 + 3) & ~3;
+  // window bits 2*N*G plus up to 31 bits of misalignment, up to 3 lead words
+  // before the window, one word of shift (G = 16) and one spare word
+  return (((2 * N * G + 31 + 31) >> 5) + 3 + 1 + 1 + 3) & ~3;
 }
 
 // Compile-time stream count GC (0: runtime p.G).  With GC = 16 a sample-time
-// group is exactly one 32-bit word (a sample pair is one 64-bit load when
-// the window starts on an even word); with GC = 32 it is two words.
+// group is exactly one 32-bit word (a sample pair is one aligned 64-bit
+// load: the staging puts the window's first word at an even index); with
+// GC = 32 it is two words.
 template <int GC>
 __device__ __forceinline__ void load_pair(const uint32_t* __restrict__ wsl, int boff, int G, int m, int j,
-                                          bool even, uint32_t& c0, uint32_t& c1) {
+                                          uint32_t& c0, uint32_t& c1) {
   if constexpr (GC == 16) {
-    uint32_t w0, w1;
-    if (even) {
-      const uint2 w = *reinterpret_cast<const uint2*>(wsl + 2 * m);
-      w0 = w.x;
-      w1 = w.y;
-    } else {
-      w0 = wsl[2 * m];
-      w1 = wsl[2 * m + 1];
-    }
-    c0 = (w0 >> (2 * j)) & 3u;
-    c1 = (w1 >> (2 * j)) & 3u;
+    // the staging put the window's first word at an even index
+    const uint2 w = *reinterpret_cast<const uint2*>(wsl + 2 * m);
+    c0 = (w.x >> (2 * j)) & 3u;
+    c1 = (w.y >> (2 * j)) & 3u;
   } else if constexpr (GC == 32) {
     const int q = 4 * m + (j >> 4);
     c0 = (wsl[q] >> (2 * (j & 15))) & 3u;
@@ -413,15 +408,27 @@ k_fstage(FParams p, int slots, int wslot) {
     // read from the 16-byte aligned word a0 = w0 & ~3 onwards (dst[q] = word
     // a0 + q), single words at the end of the data
     if (tid == 0) s_ok[sl] = ok ? 1 : 0;
-    uint32_t* dst = wbuf + sl * wslot;
     const int lead = (int)(w0 & 3);
+    // GC = 16: one word per sample time; word w0 goes to an even index so
+    // that every sample pair is one aligned 64-bit load (odd leads shift the
+    // copy by one word, stored word by word)
+    const int shift = (GC == 16) ? (lead & 1) : 0;
+    uint32_t* dst = wbuf + sl * wslot + shift;
     const int64_t a0 = w0 - lead;
     const int ntot = nw + lead;
     const int nvec = ntot >> 2;
     const uint4* src4 = reinterpret_cast<const uint4*>(sv.words + a0);
     for (int q = tid; q < nvec; q += blockDim.x) {
       if (a0 + 4 * q + 4 <= sv.nwords) {
-        reinterpret_cast<uint4*>(dst)[q] = __ldg(src4 + q);
+        const uint4 x = __ldg(src4 + q);
+        if (shift) {
+          dst[4 * q] = x.x;
+          dst[4 * q + 1] = x.y;
+          dst[4 * q + 2] = x.z;
+          dst[4 * q + 3] = x.w;
+        } else {
+          reinterpret_cast<uint4*>(dst)[q] = x;
+        }
       } else {
         for (int u = 0; u < 4; ++u)
           if (a0 + 4 * q + u < sv.nwords) dst[4 * q + u] = __ldg(&sv.words[a0 + 4 * q + u]);
@@ -429,7 +436,7 @@ k_fstage(FParams p, int slots, int wslot) {
     }
     for (int q = 4 * nvec + tid; q < ntot; q += blockDim.x)
       if (a0 + q < sv.nwords) dst[q] = __ldg(&sv.words[a0 + q]);
-    if (tid == 0) s_boff[sl] = boff + 32 * lead;  // bit offset from word a0
+    if (tid == 0) s_boff[sl] = boff + 32 * (lead + shift);  // bit offset from the slot's first word
   }
   __syncthreads();
 
@@ -442,9 +449,8 @@ k_fstage(FParams p, int slots, int wslot) {
     const bool ok = active && s_ok[sl];
     const int boff = s_boff[sl];
     // for GC = 16 / 32 the window starts on a word boundary: skip the lead
-    // words; a sample pair is then one 64-bit load when that start is even
+    // (and shift) words
     const uint32_t* wsl = wbuf + sl * wslot + (GC ? (boff >> 5) : 0);
-    const bool even = ((boff >> 5) & 1) == 0;
 
     // ---- pass 0: unpack straight into registers (NS = 1, no twiddles);
     //      the transform of a block that is not valid is skipped ----
@@ -457,7 +463,7 @@ k_fstage(FParams p, int slots, int wslot) {
         for (int r = 0; r < R0; ++r) {
           const int m = jj + r * (L / R0);
           uint32_t c0, c1;
-          load_pair<GC>(wsl, boff, G, m, j, even, c0, c1);
+          load_pair<GC>(wsl, boff, G, m, j, c0, c1);
           v[u][r] = s_lut16[c0 | (c1 << 2)];
         }
       }
@@ -516,8 +522,17 @@ __device__ __forceinline__ void load_pair_g(const StationView& sv, int64_t rel, 
                                             uint32_t& c0, uint32_t& c1) {
   if constexpr (GC == 16) {
     const int64_t w = rel + 2 * m;  // one word per sample-time group
-    c0 = (__ldg(&sv.words[w]) >> (2 * j)) & 3u;
-    c1 = (__ldg(&sv.words[w + 1]) >> (2 * j)) & 3u;
+    uint32_t w0, w1;
+    if ((rel & 1) == 0) {  // the pair is one aligned 64-bit load
+      const uint2 x = __ldg(reinterpret_cast<const uint2*>(sv.words + w));
+      w0 = x.x;
+      w1 = x.y;
+    } else {
+      w0 = __ldg(&sv.words[w]);
+      w1 = __ldg(&sv.words[w + 1]);
+    }
+    c0 = (w0 >> (2 * j)) & 3u;
+    c1 = (w1 >> (2 * j)) & 3u;
   } else {
     const int64_t bit = 2 * ((rel + 2 * m) * G + j);
     c0 = (__ldg(&sv.words[bit >> 5]) >> (bit & 31)) & 3u;

@@ -111,6 +111,17 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, 
   return false;
 }
 
+// Named barrier 1 over the 128 epilogue threads, returning the OR of v.
+__device__ __forceinline__ bool bar_or_128(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{ .reg .pred p, q; setp.ne.u32 q, %1, 0; bar.red.or.pred p, 1, 128, q; selp.u32 %0, 1, 0, p; }"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
 }  // namespace
 
 template <bool FP8>
@@ -207,6 +218,11 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
     }
   } else {
     // ---- epilogue warps 0..3: TMEM lane quadrant = warp ----
+    // V_ab of the item's W channels go to a shared stage [channel][baseline]
+    // (every element written once), then out to the partial sums as
+    // coalesced 16-byte vector reductions: the item's partials are one
+    // contiguous run of W * nbl complex values.
+    float2* stage = reinterpret_cast<float2*>(ring + kStages2 * kPairBytes);
     const int r = warp * 32 + lane;
     const bool re_lane = ((lane & 1) == 0) && r < rows_valid;
     const int a = (r >> 1) % S;
@@ -217,40 +233,59 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
     const int q0 = (2 * S * cmin) / 32, q1 = (warp * 32 < rows_valid) ? (2 * S * (cmax + 1) - 1) / 32 : -1;
     for (int n = 0; n < my_items; ++n) {
       const int ab = n & 1;
-      if (!mbar_wait_abort(&s_acc_full[ab], (n >> 1) & 1, &s_abort)) { s_abort = 1; break; }
+      const bool timed_out = !mbar_wait_abort(&s_acc_full[ab], (n >> 1) & 1, &s_abort);
+      // the four epilogue warps share named barriers below, so they stop
+      // together: a barrier OR over their timeouts and the abort flag
+      if (bar_or_128(timed_out || s_abort)) {
+        s_abort = 1;
+        break;
+      }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int item = blockIdx.x + n * gridDim.x;
       const int g = item / p.nslice;
       const int c0 = (item - g * p.nslice) * W;
+      const int nch = min(W, nchan - c0);
 #pragma unroll 1
       for (int grp = 0; grp < 2; ++grp) {
-        const int k = c0 + grp * cpt + cl;
-        float2* dst = p.part + ((size_t)g * nchan + (k < nchan ? k : 0)) * nbl;
-        const bool mine = re_lane && k < nchan;
+        const int kc = grp * cpt + cl;  // channel within the item
+        const bool mine = re_lane && c0 + kc < nchan;
+        float2* srow = stage + (size_t)kc * nbl;
 #pragma unroll 1
         for (int q = q0; q <= q1; ++q) {
           uint32_t v[32];
           tmem_ld32(taddr + ((uint32_t)(warp * 32) << 16) + ab * 256 + grp * 128 + q * 32, v);
+          // column pair jj = q*16 + i holds (channel clj, station b) = divmod(jj, S)
+          int clj = (q * 16) / S;
+          int b = q * 16 - clj * S;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const float m0 = __uint_as_float(v[2 * i]), m1 = __uint_as_float(v[2 * i + 1]);
             const float n0 = __shfl_down_sync(0xffffffffu, m0, 1);
             const float n1 = __shfl_down_sync(0xffffffffu, m1, 1);
-            const int j = q * 32 + 2 * i;
-            const int clj = (j >> 1) / S;
-            const int b = (j >> 1) % S;
-            if (mine && clj == cl && b >= a) {
-              // each partial-sum element gets exactly one add per launch, so a
-              // fire-and-forget reduction keeps the sums deterministic
-              float* o = reinterpret_cast<float*>(dst + bl_index(a, b, S));
-              atomicAdd(o, m0 + n1);
-              atomicAdd(o + 1, n0 - m1);
+            if (mine && clj == cl && b >= a) srow[bl_index(a, b, S)] = make_float2(m0 + n1, n0 - m1);
+            if (++b == S) {
+              b = 0;
+              ++clj;
             }
           }
         }
       }
+      // the accumulator has been read: hand it back to the MMA issuer
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_acc_empty[ab])) : "memory");
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // stage complete
+      // each partial-sum element gets exactly one add per launch, so the
+      // fire-and-forget reductions keep the sums deterministic
+      float* dst = reinterpret_cast<float*>(p.part + ((size_t)g * nchan + c0) * nbl);
+      const float* src = reinterpret_cast<const float*>(stage);
+      const int nf = nch * nbl * 2;  // a multiple of 4: nch is even
+      for (int e = 4 * r; e < nf; e += 4 * 128) {
+        const float4 x = *reinterpret_cast<const float4*>(src + e);
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst + e), "f"(x.x), "f"(x.y), "f"(x.z),
+                     "f"(x.w)
+                     : "memory");
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");  // stage free for the next item
     }
   }
 
@@ -263,7 +298,10 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
 cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
   const int nitems = p.G * p.nslice;
   if (nitems <= 0 || p.NKT <= 0) return cudaSuccess;
-  const size_t smem = 1024 + (size_t)kStages2 * kPairBytes;
+  // the bulk-copy ring plus the epilogue's stage of W * nbl complex values
+  // (at most 64 (S + 1) of them: 33,280 bytes at 64 stations)
+  const size_t smem = 1024 + (size_t)kStages2 * kPairBytes + (size_t)p.W * nbl_of(p.S) * sizeof(float2);
+  if (p.W % 2 || p.nchan % 2 || smem > 227 * 1024) return cudaErrorInvalidValue;
   const int grid = nitems < sm_count ? nitems : sm_count;
   if (p.fp8) {
     cudaError_t e = cudaFuncSetAttribute(k_xmma2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
