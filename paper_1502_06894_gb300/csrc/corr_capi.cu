@@ -35,6 +35,7 @@ struct Station {
   size_t len = 0;           // bytes present
   const uint8_t* ext = nullptr;  // attached (caller-owned) device bytes
   bool attached = false;
+  bool host = false;        // attached bytes live in pinned host memory
   int64_t sample0 = 0;
   bool started = false;     // a push or attach happened
   std::vector<Seg> segs;
@@ -425,6 +426,7 @@ static int upload_model(corr_t* h) {
     StationView& v = views[s];
     memset(&v, 0, sizeof(v));
     v.words = reinterpret_cast<const uint32_t*>(station_ptr(x));
+    v.host = x.host ? 1 : 0;
     v.nwords = (int64_t)(x.len / 4);
     v.sample0 = x.sample0;
     v.ngroups = station_groups(h, x);
@@ -933,6 +935,7 @@ int corr_attach_samples_host(corr_t* h, int station, const void* host_bytes, siz
   s.dbuf = nullptr;
   s.cap = 0;
   s.ext = (const uint8_t*)at.devicePointer;  // the device-side address of the pinned pages
+  s.host = true;
   s.len = nbytes;
   s.attached = true;
   s.started = true;
@@ -995,6 +998,7 @@ int corr_reset(corr_t* h) {
     if (s.attached) {
       s.ext = nullptr;
       s.attached = false;
+      s.host = false;
       s.len = 0;
     } else {
       s.len = 0;

@@ -17,6 +17,7 @@ struct StationView {
   int64_t nwords;    // whole words present
   int64_t sample0;   // station sample index of the first sample-time group
   int64_t ngroups;   // sample-time groups present (for validity)
+  int host;          // 1: the words are pinned host memory read over the host link
 };
 
 constexpr int kMaxStations = 256;

@@ -133,6 +133,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     views[s].nwords = (int64_t)(d->nbytes[s] / 4);
     views[s].sample0 = d->first_sample[s];
     views[s].ngroups = (int64_t)((d->nbytes[s] * 4) / (size_t)G);
+    views[s].host = 0;
   }
   std::vector<float2> tw(N);
   for (int m = 0; m < N; ++m) {

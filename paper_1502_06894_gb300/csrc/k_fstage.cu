@@ -25,6 +25,8 @@
 #include "corr_internal.cuh"
 
 #include <cuda_fp8.h>
+
+#include <algorithm>
 #include <math.h>
 
 namespace corr {
@@ -319,6 +321,100 @@ __host__ __device__ inline int wslot_words(int N, int G) {
   return (((2 * N * G + 31 + 31) >> 5) + 3 + 1 + 1 + 3) & ~3;
 }
 
+// Asynchronous global -> shared copies (LDGSTS) for the window staging.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage the packed windows of `nslots` blocks (chunk blocks bb0...) into
+// wbuf (slot stride wslot words) with asynchronous copies from device memory
+// (plain loads from pinned host memory): 16-byte copies where the words lie
+// inside the station's data, single words at its end.
+// The copy of slot sl starts at the 16-byte aligned word a0 = w0 & ~3; with
+// GC = 16 (one word per sample time) word w0 goes to an even index so that
+// every sample pair is one aligned 64-bit load (odd leads are copied word by
+// word, one word further on).  s_ok / s_boff receive each slot's validity
+// and the bit offset of its window from the slot's first word.
+template <int L, int GC>
+__device__ __forceinline__ void stage_windows(const FParams& p, const StationView& sv, int s, int G, int bb0,
+                                              int nslots, uint32_t* wbuf, int wslot, int* s_ok, int* s_boff) {
+  constexpr int N = 2 * L;
+  const int tid = threadIdx.x;
+  for (int sl = 0; sl < nslots; ++sl) {
+    const int d = p.blk0 + bb0 + sl;
+    const bool ok = p.valid[(size_t)s * p.ld + d] != 0;
+    int64_t w0 = 0;
+    int boff = 0, nw = 0;
+    if (ok) {
+      const int64_t rel = p.start[(size_t)s * p.ld + d] - sv.sample0;
+      const int64_t bit0 = 2 * rel * G;
+      w0 = bit0 >> 5;
+      boff = (int)(bit0 & 31);
+      nw = (boff + 2 * N * G + 31) >> 5;
+      if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);
+    }
+    const int lead = (int)(w0 & 3);
+    const int shift = (GC == 16) ? (lead & 1) : 0;
+    uint32_t* dst = wbuf + sl * wslot + shift;
+    const int64_t a0 = w0 - lead;
+    const int ntot = nw + lead;
+    const int nvec = ntot >> 2;
+    if (sv.host) {
+      // pinned host memory over the host link: plain 16-byte loads (they
+      // keep more of the link's requests in flight than the async copies)
+      const uint4* src4 = reinterpret_cast<const uint4*>(sv.words + a0);
+      for (int q = tid; q < nvec; q += blockDim.x) {
+        if (a0 + 4 * q + 4 <= sv.nwords) {
+          const uint4 x = __ldg(src4 + q);
+          if (shift) {
+            dst[4 * q] = x.x;
+            dst[4 * q + 1] = x.y;
+            dst[4 * q + 2] = x.z;
+            dst[4 * q + 3] = x.w;
+          } else {
+            reinterpret_cast<uint4*>(dst)[q] = x;
+          }
+        } else {
+          for (int u = 0; u < 4; ++u)
+            if (a0 + 4 * q + u < sv.nwords) dst[4 * q + u] = __ldg(&sv.words[a0 + 4 * q + u]);
+        }
+      }
+      for (int q = 4 * nvec + tid; q < ntot; q += blockDim.x)
+        if (a0 + q < sv.nwords) dst[q] = __ldg(&sv.words[a0 + q]);
+    } else {
+      for (int q = tid; q < nvec; q += blockDim.x) {
+        if (a0 + 4 * q + 4 <= sv.nwords) {
+          if (shift) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cp_async4(dst + 4 * q + u, sv.words + a0 + 4 * q + u);
+          } else {
+            cp_async16(dst + 4 * q, sv.words + a0 + 4 * q);
+          }
+        } else {
+          for (int u = 0; u < 4; ++u)
+            if (a0 + 4 * q + u < sv.nwords) cp_async4(dst + 4 * q + u, sv.words + a0 + 4 * q + u);
+        }
+      }
+      for (int q = 4 * nvec + tid; q < ntot; q += blockDim.x)
+        if (a0 + q < sv.nwords) cp_async4(dst + q, sv.words + a0 + q);
+    }
+    if (tid == 0) {
+      s_ok[sl] = ok ? 1 : 0;
+      s_boff[sl] = boff + 32 * (lead + shift);
+    }
+  }
+}
+
 // Compile-time stream count GC (0: runtime p.G).  With GC = 16 a sample-time
 // group is exactly one 32-bit word (a sample pair is one aligned 64-bit
 // load: the staging puts the window's first word at an even index); with
@@ -357,7 +453,7 @@ template <int L> struct MinBlocksTC {
 
 template <int L, int GC>
 __global__ void __launch_bounds__(Groups<L>::T * Groups<L>::NGRP, MinBlocks<L>::v)
-k_fstage(FParams p, int slots, int wslot) {
+k_fstage(FParams p, int slots, int wslot, int nseq) {
   using P = Plan<L>;
   constexpr int T = P::T;
   constexpr int NGRP = Groups<L>::NGRP;
@@ -380,121 +476,90 @@ k_fstage(FParams p, int slots, int wslot) {
   const int G = GC ? GC : p.G;
   const StationView sv = p.st[s];
 
-  const int bb0 = blockIdx.x * slots;
-  const int nslots = min(slots, p.CB - bb0);
-  if (nslots <= 0) return;
+  // this CTA: nseq steps of `slots` blocks each, from chunk block `first`;
+  // with nseq > 1 the windows of step it+1 are copied (asynchronously, into
+  // the other half of a double buffer) while step it is transformed
+  const int first = blockIdx.x * nseq * slots;
+  if (first >= p.CB) return;
 
-  __shared__ int s_boff[64];
-  __shared__ int s_ok[64];
+  __shared__ int s_boff[2][64];
+  __shared__ int s_ok[2][64];
   __shared__ float2 s_lut16[16];
   __shared__ float2 s_tw[Tw<L>::size];
   fill_tables<L, LastRadix<L>::v>(s_lut16, s_tw, p);
 
-  // ---- stage the windows of this CTA's blocks (16-byte loads where the
-  //      words lie inside the station's data, single words at its end) ----
-  for (int sl = 0; sl < nslots; ++sl) {
-    const int d = p.blk0 + bb0 + sl;
-    const bool ok = p.valid[(size_t)s * p.ld + d] != 0;
-    int64_t w0 = 0;
-    int boff = 0, nw = 0;
-    if (ok) {
-      const int64_t rel = p.start[(size_t)s * p.ld + d] - sv.sample0;
-      const int64_t bit0 = 2 * rel * G;
-      w0 = bit0 >> 5;
-      boff = (int)(bit0 & 31);
-      nw = (boff + 2 * N * G + 31) >> 5;
-      if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);
-    }
-    // read from the 16-byte aligned word a0 = w0 & ~3 onwards (dst[q] = word
-    // a0 + q), single words at the end of the data
-    if (tid == 0) s_ok[sl] = ok ? 1 : 0;
-    const int lead = (int)(w0 & 3);
-    // GC = 16: one word per sample time; word w0 goes to an even index so
-    // that every sample pair is one aligned 64-bit load (odd leads shift the
-    // copy by one word, stored word by word)
-    const int shift = (GC == 16) ? (lead & 1) : 0;
-    uint32_t* dst = wbuf + sl * wslot + shift;
-    const int64_t a0 = w0 - lead;
-    const int ntot = nw + lead;
-    const int nvec = ntot >> 2;
-    const uint4* src4 = reinterpret_cast<const uint4*>(sv.words + a0);
-    for (int q = tid; q < nvec; q += blockDim.x) {
-      if (a0 + 4 * q + 4 <= sv.nwords) {
-        const uint4 x = __ldg(src4 + q);
-        if (shift) {
-          dst[4 * q] = x.x;
-          dst[4 * q + 1] = x.y;
-          dst[4 * q + 2] = x.z;
-          dst[4 * q + 3] = x.w;
-        } else {
-          reinterpret_cast<uint4*>(dst)[q] = x;
-        }
-      } else {
-        for (int u = 0; u < 4; ++u)
-          if (a0 + 4 * q + u < sv.nwords) dst[4 * q + u] = __ldg(&sv.words[a0 + 4 * q + u]);
-      }
-    }
-    for (int q = 4 * nvec + tid; q < ntot; q += blockDim.x)
-      if (a0 + q < sv.nwords) dst[q] = __ldg(&sv.words[a0 + q]);
-    if (tid == 0) s_boff[sl] = boff + 32 * (lead + shift);  // bit offset from the slot's first word
-  }
-  __syncthreads();
+  stage_windows<L, GC>(p, sv, s, G, first, min(slots, p.CB - first), wbuf, wslot, s_ok[0], s_boff[0]);
+  cp_async_commit();
+  for (int it = 0; it < nseq; ++it) {
+    const int bb0 = first + it * slots;
+    if (bb0 >= p.CB) break;  // uniform over the CTA
+    const int nslots = min(slots, p.CB - bb0);
+    const int nb = it & 1;
+    if (it + 1 < nseq && bb0 + slots < p.CB)
+      stage_windows<L, GC>(p, sv, s, G, bb0 + slots, min(slots, p.CB - bb0 - slots), wbuf + (nb ^ 1) * slots * wslot,
+                           wslot, s_ok[nb ^ 1], s_boff[nb ^ 1]);
+    cp_async_commit();
+    cp_async_wait<1>();  // this step's windows have landed (the next step's may still fly)
+    __syncthreads();
+    uint32_t* wcur = wbuf + nb * slots * wslot;
 
-  const int ntasks = nslots * G;
-  for (int base = 0; base < ntasks; base += NGRP) {
-    const int task = base + grp;
-    const bool active = task < ntasks;
-    const int sl = active ? task / G : 0;
-    const int j = active ? task - sl * G : 0;
-    const bool ok = active && s_ok[sl];
-    const int boff = s_boff[sl];
-    // for GC = 16 / 32 the window starts on a word boundary: skip the lead
-    // (and shift) words
-    const uint32_t* wsl = wbuf + sl * wslot + (GC ? (boff >> 5) : 0);
+    const int ntasks = nslots * G;
+    for (int base = 0; base < ntasks; base += NGRP) {
+      const int task = base + grp;
+      const bool active = task < ntasks;
+      const int sl = active ? task / G : 0;
+      const int j = active ? task - sl * G : 0;
+      const bool ok = active && s_ok[nb][sl];
+      const int boff = s_boff[nb][sl];
+      // for GC = 16 / 32 the window starts on a word boundary: skip the lead
+      // (and shift) words
+      const uint32_t* wsl = wcur + sl * wslot + (GC ? (boff >> 5) : 0);
 
-    // ---- pass 0: unpack straight into registers (NS = 1, no twiddles);
-    //      the transform of a block that is not valid is skipped ----
-    if (ok) {
-      float2 v[PER0][R0];
+      // ---- pass 0: unpack straight into registers (NS = 1, no twiddles);
+      //      the transform of a block that is not valid is skipped ----
+      if (ok) {
+        float2 v[PER0][R0];
 #pragma unroll
-      for (int u = 0; u < PER0; ++u) {
-        const int jj = t + u * T;
+        for (int u = 0; u < PER0; ++u) {
+          const int jj = t + u * T;
 #pragma unroll
-        for (int r = 0; r < R0; ++r) {
-          const int m = jj + r * (L / R0);
-          uint32_t c0, c1;
-          load_pair<GC>(wsl, boff, G, m, j, c0, c1);
-          v[u][r] = s_lut16[c0 | (c1 << 2)];
+          for (int r = 0; r < R0; ++r) {
+            const int m = jj + r * (L / R0);
+            uint32_t c0, c1;
+            load_pair<GC>(wsl, boff, G, m, j, c0, c1);
+            v[u][r] = s_lut16[c0 | (c1 << 2)];
+          }
         }
+#pragma unroll
+        for (int u = 0; u < PER0; ++u) {
+          const int jj = t + u * T;
+          dft_reg<R0>(v[u]);
+#pragma unroll
+          for (int r = 0; r < R0; ++r) fbuf[padp<R0>(jj * R0 + r)] = v[u][r];
+        }
+        gsync<T>(grp);
+        if constexpr (P::R1 > 1)
+          stockham_pass<L, P::R1, P::R0, T, P::R0>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
+        if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0>(fbuf, t, grp, p.twN);
       }
-#pragma unroll
-      for (int u = 0; u < PER0; ++u) {
-        const int jj = t + u * T;
-        dft_reg<R0>(v[u]);
-#pragma unroll
-        for (int r = 0; r < R0; ++r) fbuf[padp<R0>(jj * R0 + r)] = v[u][r];
+
+      // ---- real split, rotation, store ----
+      if (active) {
+        const int d = p.blk0 + bb0 + sl;
+        const int bb = bb0 + sl;
+        const float delta = ok ? p.delta[(size_t)s * p.ld + d] : 0.f;
+        const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
+        const size_t obase = (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
+        if (p.out_kind == 1)
+          split_rotate_store<L, T, R0, 1>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
+        else if (p.out_kind == 2)
+          split_rotate_store<L, T, R0, 2>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
+        else
+          split_rotate_store<L, T, R0, 0>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
       }
       gsync<T>(grp);
-      if constexpr (P::R1 > 1)
-        stockham_pass<L, P::R1, P::R0, T, P::R0>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
-      if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0>(fbuf, t, grp, p.twN);
     }
-
-    // ---- real split, rotation, store ----
-    if (active) {
-      const int d = p.blk0 + bb0 + sl;
-      const int bb = bb0 + sl;
-      const float delta = ok ? p.delta[(size_t)s * p.ld + d] : 0.f;
-      const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
-      const size_t obase = (((size_t)j * p.CB + bb) * p.S + s) * (size_t)L;
-      if (p.out_kind == 1)
-        split_rotate_store<L, T, R0, 1>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
-      else if (p.out_kind == 2)
-        split_rotate_store<L, T, R0, 2>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
-      else
-        split_rotate_store<L, T, R0, 0>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
-    }
-    gsync<T>(grp);
+    __syncthreads();  // every read of this step's windows is done before they are overwritten
   }
 }
 
@@ -768,12 +833,28 @@ static cudaError_t launch_LG(const FParams& p, cudaStream_t st) {
   if (slots < 1) slots = 1;
   if (slots > 64) slots = 64;
   const int wslot = wslot_words(N, p.G);
-  const size_t smem = kWordsOffset<L>(NGRP) + (size_t)slots * wslot * sizeof(uint32_t);
+  const size_t one = kWordsOffset<L>(NGRP) + (size_t)slots * wslot * sizeof(uint32_t);
+  const size_t two = one + (size_t)slots * wslot * sizeof(uint32_t);
+  // Several steps per CTA (tables filled once, the next windows copied while
+  // the current ones are transformed) when the double buffer still lets the
+  // kernel keep its CTAs per SM and the grid stays at 8+ waves of them.
+  static int sm_count = 0;
+  if (!sm_count) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sm_count = 152;
+  }
+  const int64_t steps = (int64_t)((p.CB + slots - 1) / slots) * p.S;
+  int nseq = 1;
+  if ((size_t)MinBlocks<L>::v * (two + sizeof(float2) * Tw<L>::size + 1024) <= 227 * 1024)
+    nseq = (int)std::max<int64_t>(1, std::min<int64_t>(4, steps / ((int64_t)8 * MinBlocks<L>::v * sm_count)));
+  const size_t smem = nseq > 1 ? two : one;
   if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_fstage<L, GC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((p.CB + slots - 1) / slots, p.S);
-  k_fstage<L, GC><<<grid, T * NGRP, smem, st>>>(p, slots, wslot);
+  const int per_cta = slots * nseq;
+  dim3 grid((p.CB + per_cta - 1) / per_cta, p.S);
+  k_fstage<L, GC><<<grid, T * NGRP, smem, st>>>(p, slots, wslot, nseq);
   return cudaGetLastError();
 }
 
