@@ -77,6 +77,25 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest x over all ranks of the process group (the slowest
+    replica sets the step time); x itself with no group or one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_step: float, world_size: int, ms_per_step: float) -> float:
+    """Whole-job throughput of independent replicas (weak scaling): every rank
+    processes units_per_step in each step, and the step takes the slowest
+    rank's time."""
+    return units_per_step * world_size / (ms_per_step / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -489,16 +508,12 @@ def main():
         prof = c.read_profile()
         shape = c.launch_shape()
         c.close()
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev)
         return ms, prof, clocks, shape
 
     ms, prof, clocks, (cb, kz) = device_leg(corr.CORR_PREC_FP32)
     sps = samples_per_step(scan)
-    value = sps * ws / (ms / 1e3)
+    value = replica_value(sps, ws, ms)
     tc = None
     if not args.no_tc:
         ms_tc, prof_tc, clocks_tc, _ = device_leg(corr.CORR_PREC_FP16_TC)
@@ -555,7 +570,7 @@ def main():
         ft_ms, ft_n = prof_t["fstage"]
         # reduced-precision spectra: elem_bytes read per station-sample in the X step
         xt_bytes = steps * ss_step * elem_bytes
-        return {"value": sps * ws / (ms_t / 1e3), "unit": METRIC, "ms_per_step": ms_t, "dtype": dtype,
+        return {"value": replica_value(sps, ws, ms_t), "unit": METRIC, "ms_per_step": ms_t, "dtype": dtype,
                 "error_bound_rel_rms": bound, "measured_rel_rms": measured,
                 "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
                 "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
@@ -601,12 +616,7 @@ def main():
                 fn()
             torch.cuda.synchronize()
             dt = (time.perf_counter() - t0) / n
-            if ws > 1:
-                import torch.distributed as dist
-                t = torch.tensor([dt], device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                dt = float(t.item())
-            return dt
+            return max_over_ranks(dt, dev)
 
         def correlate_all(cc):
             for i in range(nint):
@@ -627,7 +637,7 @@ def main():
 
         ne = max(2, min(args.steps, 5))
         dt = timed(e2e_zero_copy, ne)
-        e2e = {"value": sps * ws / dt, "unit": METRIC, "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
+        e2e = {"value": replica_value(sps, ws, dt * 1e3), "unit": METRIC, "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": d2h,
                "ms_per_step": dt * 1e3, "steps": ne,
                "mode": "zero-copy: pinned host buffers attached, read by the F kernel over NVLink-C2C"}
         c2.close()
@@ -671,7 +681,7 @@ def main():
             c3.wait_pushes()
 
         dt = timed(e2e_copy_step, ne)
-        e2e_copy = {"value": sps * ws / dt, "unit": METRIC, "ms_per_step": dt * 1e3, "h2d_bytes_per_step": in_bytes,
+        e2e_copy = {"value": replica_value(sps, ws, dt * 1e3), "unit": METRIC, "ms_per_step": dt * 1e3, "h2d_bytes_per_step": in_bytes,
                     "mode": "copy: corr_push_samples_async pieces two integrations ahead"}
         c3.close()
 
