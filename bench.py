@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense 64-station X-step leg")
     ap.add_argument("--dense-duration", type=float, default=0.5,
                     help="seconds of the 64-station scan in the dense leg (the named scan is 4 s)")
+    ap.add_argument("--no-fringe", action="store_true", help="skip the delay-rate fringe-search leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-scan batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served leg")
     ap.add_argument("--batch-scans", type=int, default=96)
@@ -349,6 +350,37 @@ def dense_leg(args, torch, corr, dev):
     del streams
     torch.cuda.empty_cache()
     return res
+
+
+def fringe_leg(args, torch, corr, dev):
+    """Delay-rate fringe search (corr_fringe_search) of one baseline: 256
+    sub-integrations x 1024 channels, padded to 512 rate x 8192 lag bins (a
+    4x finer lag grid than the channels give), timed per call with CUDA
+    events (the call returns when its peak is on the host)."""
+    T, K, Nr, Nd = 256, 1024, 512, 8192
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    V = torch.complex(torch.randn((T, K), generator=g, device=dev), torch.randn((T, K), generator=g, device=dev))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        corr.fringe_search(V, Nr, Nd)
+    torch.cuda.synchronize()
+    n = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(n):
+        corr.fringe_search(V, Nr, Nd)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    # algorithmic bytes: V read, lag transforms written and read, map written and read (peak)
+    nbytes = 8.0 * (T * K + 2 * T * Nd + 2 * Nr * Nd)
+    flops = 5.0 * (T * Nd * np.log2(Nd) + Nd * Nr * np.log2(Nr))  # radix-2 complex FFT count
+    return {"workload": "one baseline: %d sub-integrations x %d channels -> %d rate x %d lag bins" % (T, K, Nr, Nd),
+            "ms_per_search": ms, "map_points_per_s": Nr * Nd / (ms / 1e3), "hbm_gbs": nbytes / (ms / 1e3) / 1e9,
+            "fft_gflops": flops / (ms / 1e3) / 1e9,
+            "timing": "CUDA events around %d calls; each call includes its host read of the peak" % n}
 
 
 def batch_leg(args, torch, corr, dev):
@@ -688,12 +720,15 @@ def main():
     batch = None
     served = None
     dense = None
+    fringe = None
     if rank == 0 and ws == 1:
         # free the single-scan buffers first: the mix brings its own pool
         del out, wts
         torch.cuda.empty_cache()
         if not args.no_dense:
             dense = dense_leg(args, torch, corr, dev)
+        if not args.no_fringe:
+            fringe = fringe_leg(args, torch, corr, dev)
         if not args.no_batch:
             batch = batch_leg(args, torch, corr, dev)
         if not args.no_serve:
@@ -720,7 +755,7 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
-                "dense": dense, "batch": batch, "serve": served}
+                "dense": dense, "fringe": fringe, "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist

@@ -244,6 +244,31 @@ int corr_read_profile(corr_t *h, double ms[4], int64_t launches[4]);
  * uses (valid after the first correlate call). */
 int corr_launch_shape(const corr_t *h, int *chunk_blocks, int *kz);
 
+/* ---- delay-rate fringe search ---------------------------------------------
+ *
+ * The wide-window fringe search the paper lists among the dra-DiFX features
+ * for RadioAstron (Sec. 2): a map of one baseline's visibilities over
+ * residual delay and fringe rate, and its peak.  For V[t][k] (t: one of nsub
+ * sub-integrations, k: one of nchan channels; complex64 rows of nchan, device
+ * memory, e.g. one baseline/stream of successive corr_correlate_device
+ * outputs) the map is the zero-padded two-dimensional inverse DFT,
+ * unnormalised:
+ *     M[r][l] = sum_t sum_k V[t][k] exp(+2 pi i (k l / pad_delay + t r / pad_rate)),
+ * written to dev_map (complex64 [pad_rate][pad_delay], device memory, owned
+ * by the caller).  Lag l is a delay of l * 2 nchan / pad_delay samples
+ * (l >= pad_delay / 2: l - pad_delay); rate bin r is a fringe rate of
+ * r / (pad_rate * T_sub) Hz (r >= pad_rate / 2: r - pad_rate).  The peak is
+ * the largest |M|, the smaller flat index r * pad_delay + l on ties; its rate
+ * bin, lag, amplitude and complex value (2 floats) go to the host pointers
+ * (each may be NULL).  pad_rate >= nsub and pad_delay >= nchan are powers of
+ * two <= 16384 with pad_rate * pad_delay <= 2^26 (else CORR_EINVAL).  Work
+ * space (pad_delay * nsub complex values) is taken with cudaMallocAsync on
+ * cuda_stream (NULL: the legacy default stream) and released there
+ * (CORR_ENOMEM if that fails); the call returns when the search is done
+ * (CORR_ECUDA on a CUDA error). */
+int corr_fringe_search(const float *dev_vis, int nsub, int nchan, int pad_rate, int pad_delay, float *dev_map,
+                       int *peak_rate, int *peak_lag, float *peak_amp, float *peak_value, void *cuda_stream);
+
 /* ---- correlation without device allocation -------------------------------
  *
  * The paper has no counterpart of this entry point; it exists for callers of

@@ -163,3 +163,33 @@ def unpack_codes(stream: np.ndarray, G: int, j: int, t0: int, count: int) -> np.
 
 def threads() -> int:
     return int(lib().oracle_threads())
+
+
+# ---- delay-rate fringe search (the wide-window fringe search of Sec. 2) ----
+#
+# The map of one baseline's visibilities V[t][k] (t: sub-integration, k:
+# channel) over lag l and rate bin r is the zero-padded two-dimensional
+# inverse DFT, unnormalised:
+#     M[r][l] = | sum_t sum_k V[t][k] exp(+2 pi i (k l / Nd + t r / Nr)) |,
+# l < Nd (lag l ~ l N / Nd samples, l >= Nd/2 read as l - Nd), r < Nr (fringe
+# rate r / (Nr T_sub), r >= Nr/2 read as r - Nr).  The peak is the largest
+# amplitude, the smaller flat index r * Nd + l on ties.  numpy's inverse FFT
+# (times Nr * Nd) is the library step for the double sum.
+
+def fringe_map(V: np.ndarray, pad_rate: int, pad_delay: int) -> np.ndarray:
+    """Complex delay-rate map [pad_rate][pad_delay] of V[nsub][nchan] (FP64)."""
+    V = np.asarray(V, dtype=np.complex128)
+    T, K = V.shape
+    if pad_rate < T or pad_delay < K:
+        raise ValueError("the padded sizes must cover the sub-integrations and channels")
+    pad = np.zeros((pad_rate, pad_delay), np.complex128)
+    pad[:T, :K] = V
+    return np.fft.ifft2(pad) * (pad_rate * pad_delay)
+
+
+def fringe_peak(amp: np.ndarray):
+    """(rate bin, lag bin, amplitude) of the largest amplitude; ties go to the
+    smaller flat index (numpy's argmax returns the first maximum)."""
+    i = int(np.argmax(amp))
+    r, l = np.unravel_index(i, amp.shape)
+    return int(r), int(l), float(amp[r, l])

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcorr.so")
-SOURCES = ["corr_capi.cu", "k_delay.cu", "k_fstage.cu", "k_xstage.cu", "k_finalize.cu", "k_xmma.cu", "corr_static.cu"]
+SOURCES = ["corr_capi.cu", "k_delay.cu", "k_fstage.cu", "k_xstage.cu", "k_finalize.cu", "k_xmma.cu", "corr_static.cu",
+           "k_fringe.cu"]
 HEADERS = ["corr_internal.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -81,6 +81,8 @@ _SIGS = {
     "corr_correlate_static": ([C.POINTER(CorrScanDesc), C.c_int64, _P, _P, _P], C.c_int),
     "corr_batch_run": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "corr_device_bytes": ([_H, C.POINTER(C.c_size_t)], C.c_int),
+    "corr_fringe_search": ([_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                            C.POINTER(C.c_float), _P, _P], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -351,3 +353,25 @@ def batch_run(correlators, dev_outs, dev_weights=None, stream=None) -> int:
         raise CorrError(rc, "corr_batch_run failed: " + corr_last_error(correlators[0].h).decode())
     return rc
 
+
+
+def fringe_search(vis, pad_rate: int, pad_delay: int, stream: Optional[int] = None):
+    """Delay-rate fringe search (corr_fringe_search) of one baseline's
+    visibilities vis (a CUDA complex64 tensor [nsub][nchan]).  Returns the
+    complex map (a new CUDA complex64 tensor [pad_rate][pad_delay]) and the
+    peak as (rate bin, lag, amplitude, complex value)."""
+    import torch
+    if vis.dtype != torch.complex64 or not vis.is_cuda or vis.dim() != 2:
+        raise ValueError("vis must be a CUDA complex64 tensor [nsub][nchan]")
+    vis = vis.contiguous()
+    nsub, nchan = vis.shape
+    out = torch.empty((pad_rate, pad_delay), dtype=torch.complex64, device=vis.device)
+    r, l, a = C.c_int(), C.c_int(), C.c_float()
+    val = (C.c_float * 2)()
+    if stream is None:
+        stream = torch.cuda.current_stream(vis.device).cuda_stream
+    rc = corr_fringe_search(vis.data_ptr(), int(nsub), int(nchan), int(pad_rate), int(pad_delay), out.data_ptr(),
+                            C.byref(r), C.byref(l), C.byref(a), C.cast(val, C.c_void_p), stream)
+    if rc != CORR_OK:
+        raise CorrError(rc, "corr_fringe_search")
+    return out, (r.value, l.value, a.value, complex(val[0], val[1]))
