@@ -104,10 +104,10 @@ def dist_env():
     return ws, rank, local
 
 
-def traffic_per_launch(kernel):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
-    summary table (captured at the benchmark's launch shape), else None."""
-    p = os.path.join(ROOT, "profiles", "traffic.txt")
+def profile_value(table, kernel):
+    """Per-launch figure of `kernel` from a committed ncu summary table under
+    profiles/ (captured at the benchmark's launch shape), else None."""
+    p = os.path.join(ROOT, "profiles", table)
     if not os.path.exists(p):
         return None
     for line in open(p):
@@ -115,6 +115,20 @@ def traffic_per_launch(kernel):
         if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel:
             return float(parts[1])
     return None
+
+
+def traffic_per_launch(kernel):
+    """DRAM bytes (read + write) per launch of `kernel`."""
+    return profile_value("traffic.txt", kernel)
+
+
+def issue_frac(warp_instructions, launch_s, sm_mhz):
+    """Fraction of the instruction-issue ceiling a launch reaches: its warp
+    instructions over launch time x 4 issue slots per SM per clock x the SM
+    count x the SM clock; None when an input is missing."""
+    if not warp_instructions or not launch_s or not sm_mhz:
+        return None
+    return float(warp_instructions) / (float(launch_s) * 4.0 * SM_COUNT * float(sm_mhz) * 1e6)
 
 
 def measured_peaks():
@@ -595,6 +609,11 @@ def main():
     roof.update({"kernel": kname,
                  "bytes_per_launch": d_bytes / max(d_n, 1), "flops_per_launch": d_flops / max(d_n, 1),
                  "launch_ms": t_launch * 1e3, "hbm_frac": hbm_frac, "alu_frac": alu_frac})
+    # the F step is bound by instruction issue: its warp instructions per
+    # launch (ncu) against the issue ceiling at the SM clock seen under load
+    inst = profile_value("instructions.txt", kname)
+    roof["warp_instructions"] = inst
+    roof["issue_frac"] = issue_frac(inst, t_launch, (clocks or {}).get("sm_mhz") or MAX_SM_MHZ)
     launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
     def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound, measured):
