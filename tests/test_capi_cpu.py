@@ -68,3 +68,18 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert L.corr_create(C.byref(h), 2, 1, 3, 256, 1.0) == -1
     assert L.corr_create(C.byref(h), 2, 1, 1, 256, -1.0) == -1
     assert not h.value
+
+
+def test_fringe_search_checks_arguments_before_any_device_work(lib):
+    """corr_fringe_search rejects missing buffers and pads that are not powers
+    of two, below the data, above 16384 or too large together with
+    CORR_EINVAL, before it touches the device (so this runs without a GPU)."""
+    L = C.CDLL(lib)
+    L.corr_fringe_search.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    dummy = C.c_void_p(16)  # never dereferenced: the checks fail first
+    assert L.corr_fringe_search(None, 4, 8, 4, 8, dummy, None, None, None, None, None) == -1
+    assert L.corr_fringe_search(dummy, 4, 8, 4, 8, None, None, None, None, None, None) == -1
+    assert L.corr_fringe_search(dummy, 0, 8, 4, 8, dummy, None, None, None, None, None) == -1
+    for nr, nd in ((3, 8), (4, 12), (2, 8), (4, 4), (32768, 8), (8192, 16384)):
+        assert L.corr_fringe_search(dummy, 4, 8, nr, nd, dummy, None, None, None, None, None) == -1, (nr, nd)
