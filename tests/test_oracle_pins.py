@@ -328,3 +328,183 @@ def test_fringe_delay_rate_search_with_zero_model(cfg1):
     peak, tau0, rate = best
     assert abs(tau0 - 3.7) <= 0.2, best
     assert abs(rate - 2e-6) <= 5e-8, best
+
+
+# --------------------------------------------------------------------------
+# T1b (continued): every term of the quintic delay polynomial
+
+
+def _horner_exact(coeffs, u):
+    """The polynomial's exact value in rational arithmetic (power form, not Horner)."""
+    return sum(Fraction(c) * Fraction(u) ** i for i, c in enumerate(coeffs))
+
+
+def _one_station_delays(fs, nchan, segs, b):
+    o = oracle.Oracle(1, 1, 1, nchan, fs, 64 * 2 * nchan / fs, [0.0], [segs], [np.zeros(64, np.uint8)],
+                      [-(1 << 50)], [1 << 51])
+    n, e, t, v = o.delays(b, 1)
+    return int(n[0, 0]), float(e[0, 0]), float(t[0, 0])
+
+
+def test_quintic_delay_exact_dyadic():
+    """With dyadic coefficients and block centres every step of the FP64
+    evaluation is exact, so tau must equal the exact polynomial value bit for
+    bit: a dropped or shifted term (c4, c5 included) changes it.  fs = 2^20
+    makes tau*fs + 1/2 exact, so n_b and eps are fixed exactly too."""
+    fs, nchan = float(1 << 20), 8
+    N = 2 * nchan
+    rng = np.random.default_rng(20)
+    for case in range(300):
+        b = int(rng.integers(0, 20000))
+        tc = Fraction(b * N + N // 2) / Fraction(int(fs))
+        u = Fraction(int(rng.integers(1, 32)), 8)
+        t0 = tc - u
+        # every term matters; all of them fit one 53-bit significand together
+        coeffs = [float(Fraction(int(rng.integers(-63, 64)), 1 << int(rng.integers(4, 20)))) for _ in range(6)]
+        coeffs[5] = float(Fraction(int(rng.choice([-1, 1]) * rng.integers(1, 64)), 1 << int(rng.integers(0, 8))))
+        exact = _horner_exact(coeffs, u)
+        assert Fraction(float(exact)) == exact  # representable: the evaluation has no rounding to hide a slip
+        n_b, eps, tau = _one_station_delays(fs, nchan, [synth.Segment(float(t0), tuple(coeffs))], b)
+        assert Fraction(tau) == exact, (case, coeffs, float(u))
+        want_n = math.floor(exact * int(fs) + Fraction(1, 2))
+        assert n_b == want_n
+        assert Fraction(eps) == exact - Fraction(want_n, int(fs))
+        # dropping c5 (or starting the evaluation at c4) must be visible
+        assert _horner_exact(coeffs[:5], u) != exact
+
+
+def test_quintic_delay_ties_through_all_terms():
+    """c0 placed so that tau*fs is exactly m + 1/2 (ties go up, n_b = m+1), and
+    2^-13 samples either side of it, with all six coefficients non-zero."""
+    fs, nchan = float(1 << 20), 8
+    N = 2 * nchan
+    rng = np.random.default_rng(21)
+    for case in range(60):
+        b = int(rng.integers(0, 5000))
+        tc = Fraction(b * N + N // 2) / Fraction(int(fs))
+        u = Fraction(int(rng.integers(1, 32)), 8)
+        hi = [float(Fraction(int(rng.integers(1, 64)), 1 << int(rng.integers(4, 16)))) for _ in range(5)]
+        m = int(rng.integers(-(1 << 18), 1 << 18))
+        for frac_samples, want in ((Fraction(1, 2), m + 1), (Fraction(1, 2) + Fraction(1, 8192), m + 1),
+                                   (Fraction(1, 2) - Fraction(1, 8192), m)):
+            target = (m + frac_samples) / Fraction(int(fs))
+            c0 = target - sum(Fraction(c) * u ** (i + 1) for i, c in enumerate(hi))
+            assert Fraction(float(c0)) == c0
+            coeffs = [float(c0)] + hi
+            n_b, eps, tau = _one_station_delays(fs, nchan, [synth.Segment(float(tc - u), tuple(coeffs))], b)
+            assert Fraction(tau) == target
+            assert n_b == want, (case, m, frac_samples, n_b)
+            assert Fraction(eps) == target - Fraction(want, int(fs))
+
+
+def test_quintic_delay_realistic_within_rounding_bound():
+    """Spacecraft-like quintic segments (tau ~ 1 s, rate 3e-5, 120 s segments)
+    at non-dyadic fs: tau stays within the FP64 rounding bound of the exact
+    value (Horner with one rounding per step: 6 * 2^-53 * sum |c_i u^i|), and
+    n_b follows the exact value wherever it is not within that bound of a
+    tie.  (The exact dyadic cases above fix each term; this one fixes the
+    rounding behaviour at the workloads' magnitudes.)"""
+    fs, nchan = 32e6, 512
+    N = 2 * nchan
+    rng = np.random.default_rng(22)
+    checked = 0
+    for case in range(200):
+        coeffs = (float(rng.uniform(0.3, 1.2)), float(rng.uniform(-3e-5, 3e-5)), float(rng.uniform(-1, 1) * 1e-9),
+                  float(rng.uniform(-1, 1) * 1e-12), float(rng.uniform(-1, 1) * 1e-15),
+                  float(rng.uniform(-1, 1) * 1e-18))
+        t0 = -float(rng.uniform(0.0, 120.0))
+        b = int(rng.integers(0, 300000))
+        tc = Fraction(b * N + N // 2) / Fraction(fs)
+        u = Fraction(float(tc)) - Fraction(t0)  # the oracle forms t_c in FP64, then t_c - t0
+        u = Fraction(float(u))
+        exact = _horner_exact(coeffs, u)
+        n_b, eps, tau = _one_station_delays(fs, nchan, [synth.Segment(t0, coeffs)], b)
+        terms = [abs(Fraction(c) * u ** i) for i, c in enumerate(coeffs)]
+        bound = 6 * Fraction(1, 1 << 53) * sum(terms)
+        assert abs(Fraction(tau) - exact) <= bound
+        x = exact * Fraction(fs) + Fraction(1, 2)
+        if abs(x - round(x)) > 4 * bound * Fraction(fs):
+            assert n_b == math.floor(x)
+            checked += 1
+    assert checked > 150
+
+
+# --------------------------------------------------------------------------
+# D6: integration membership when fs*tint is not a whole number of blocks
+
+
+def test_ragged_integration_membership():
+    """fs*tint = 120 samples = 7.5 blocks of 16: block b belongs to integration
+    floor(b*N / (fs*tint)), so integrations hold 8, 7, 8, 7 blocks.  The
+    weights must be those brute-force counts and each integration's
+    unnormalised sum must be exactly the sum of its own blocks' products."""
+    fs, nchan = 1024.0, 8
+    N = 2 * nchan
+    spi = 120
+    tint = spi / fs
+    nint = 4
+    S = 2
+    T = nint * spi + 4 * N
+    rng = np.random.default_rng(7)
+    streams = [synth.pack(rng.integers(0, 4, (T, 1)).astype(np.uint8)) for _ in range(S)]
+    segs = [[synth.Segment(0.0, (0.0,) * 6)], [synth.Segment(0.0, (3.0 / fs, 0, 0, 0, 0, 0))]]
+    o = oracle.Oracle(S, 1, 1, nchan, fs, tint, [0.0], segs, streams, [0, 0], [T, T])
+    vis, w = o.correlate(0, nint)
+    nblocks = -(-nint * spi // N)
+    member = [math.floor(Fraction(b * N, spi)) for b in range(nblocks)]
+    counts = [member.count(i) for i in range(nint)]
+    assert counts == [8, 7, 8, 7]
+    for i in range(nint):
+        assert w[i].tolist() == [counts[i]] * 3
+        acc = np.zeros((3, nchan), complex)
+        for b in (b for b in range(nblocks) if member[b] == i):
+            X = [o.spectrum(s, 0, b)[0] for s in range(S)]
+            acc += np.array([X[0] * np.conj(X[0]), X[0] * np.conj(X[1]), X[1] * np.conj(X[1])])
+        got = vis[i, :, 0] * (counts[i] * N)
+        assert np.max(np.abs(got - acc)) <= 1e-12 * np.max(np.abs(acc))
+
+
+# --------------------------------------------------------------------------
+# D5: a block is valid exactly when every sample of its window exists
+
+
+@pytest.mark.parametrize("lead", [0, 1])
+@pytest.mark.parametrize("tail", [0, 1])
+def test_validity_at_the_data_edges(lead, tail):
+    """A station whose data start exactly at block 0's window (lead = 0) or one
+    sample later (lead = 1), and end exactly at block 6's window end
+    (tail = 0) or one sample earlier (tail = 1).  The first and last blocks
+    are valid only when all their samples exist, and a valid edge block's
+    spectrum is the DFT of exactly the first (last) N samples present."""
+    fs, nchan, m = 1024.0, 8, 5
+    N = 2 * nchan
+    first = m + lead              # window of block 0 starts at station sample m
+    end = 6 * N + m + N - tail    # window of block 6 ends at 6N + m + N
+    T = end - first
+    rng = np.random.default_rng(8 + 2 * lead + tail)
+    codes = rng.integers(0, 4, (T, 1)).astype(np.uint8)
+    stream = synth.pack(codes)
+    segs = [[synth.Segment(0.0, (m / fs, 0, 0, 0, 0, 0))]]
+    o = oracle.Oracle(1, 1, 1, nchan, fs, 8 * N / fs, [0.0], segs, [stream], [first], [T])
+    n, e, t, v = o.delays(0, 8)
+    assert n[0].tolist() == [m] * 8
+    want = [1] * 8
+    want[7] = 0                   # block 7 needs samples beyond block 6's window end
+    if lead:
+        want[0] = 0
+    if tail:
+        want[6] = 0
+    assert v[0].tolist() == want
+    k = np.arange(nchan)
+    D = np.exp(-2j * np.pi * np.outer(k, np.arange(N)) / N)
+    X0, ok0 = o.spectrum(0, 0, 0)
+    X6, ok6 = o.spectrum(0, 0, 6)
+    assert ok0 == (not lead) and ok6 == (not tail)
+    if not lead:
+        ref = D @ LUT[my_codes(stream, 1, 0, 0, N)]
+        assert np.max(np.abs(X0 - ref)) < 1e-12 * np.max(np.abs(ref))
+    if not tail:
+        ref = D @ LUT[my_codes(stream, 1, 0, T - N, N)]
+        assert np.max(np.abs(X6 - ref)) < 1e-12 * np.max(np.abs(ref))
+    else:
+        assert np.all(X6 == 0)
