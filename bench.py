@@ -43,6 +43,8 @@ import numpy as np  # noqa: E402
 WORKLOAD = "cfg2: 10 stations (1 space + 9 ground), 8 subbands x 16 MHz, 2 pols, 2-bit, 10 s, 1024 channels, 1 s integrations"
 METRIC = "station-samples/s"
 CPU_SAMPLE_S = 0.1
+DENSE_SAMPLE_S = 0.004   # 64-station sample for the measured error (16 of its 32 streams)
+DENSE_SAMPLE_STREAMS = 16
 # 2-bit code probabilities of +-0.98 sigma quantisation of a unit Gaussian
 P_OUTER = 0.5 * (1.0 - 0.6729121)
 FALLBACK_HBM_GBS = 6800.0
@@ -216,30 +218,60 @@ def samples_per_step(scan):
     return scan.stations * scan.G * int(round(scan.duration / scan.tint)) * int(round(scan.fs * scan.tint))
 
 
-def cpu_oracle_sample(scan, host_streams, threads_hint=None):
-    """Time the FP64 oracle on the first CPU_SAMPLE_S seconds of the scan as
-    one integration (all stations and streams).  Returns (samples/s, cores, secs)."""
+def cpu_oracle_sample(scan, host_streams, seconds=CPU_SAMPLE_S, nj=None):
+    """Time the FP64 oracle on the first `seconds` of the scan as one
+    integration (all stations; the first nj streams, default all).
+    Returns (samples/s, cores, secs, min weight, visibilities [nbl, nj, nchan])."""
     import oracle
-    spi = int(round(scan.fs * CPU_SAMPLE_S))
+    spi = int(round(scan.fs * seconds))
+    nj = scan.G if nj is None else nj
     ns = []
     streams = []
     for s in range(scan.stations):
         n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
         ns.append(n)
         streams.append(np.ascontiguousarray(host_streams[s][: n * scan.G // 4]))
-    o = oracle.Oracle(scan.stations, scan.nsub, scan.npol, scan.nchan, scan.fs, CPU_SAMPLE_S, scan.nu0,
+    o = oracle.Oracle(scan.stations, scan.nsub, scan.npol, scan.nchan, scan.fs, seconds, scan.nu0,
                       scan.polys, streams, scan.sample0, ns)
     t0 = time.perf_counter()
-    vis, w = o.correlate(0, 1)
+    vis, w = o.correlate(0, 1, 0, nj)
     dt = time.perf_counter() - t0
     nblk = -(-spi // scan.N)
-    samples = scan.stations * scan.G * nblk * scan.N
-    cores = min(oracle.threads(), scan.G)
-    return samples / dt, cores, dt, float(w.min())
+    samples = scan.stations * nj * nblk * scan.N
+    cores = min(oracle.threads(), nj)
+    return samples / dt, cores, dt, float(w.min()), vis[0]
 
 
-def host_stream_prefix(dev_streams, scan):
-    spi = int(round(scan.fs * CPU_SAMPLE_S))
+def sample_errors(corr, scan, host_streams, ref, seconds=CPU_SAMPLE_S, precisions=(0, 1, 2)):
+    """Largest relative RMS per baseline of the GPU path (through the C ABI,
+    host-pushed samples) against the oracle's visibilities `ref` of the same
+    sample, per precision: the measured error of the benchmarked workload."""
+    spi = int(round(scan.fs * seconds))
+    nj = ref.shape[1]
+    out = {}
+    for prec in precisions:
+        c = corr.Correlator(scan.stations, scan.nsub, scan.npol, scan.nchan, seconds, fs=scan.fs)
+        for sb, nu in enumerate(scan.nu0):
+            if nu:
+                c.set_sky_freq(sb, nu)
+        c.set_precision(prec)
+        for s, segs in enumerate(scan.polys):
+            for g in segs:
+                c.set_delay_poly(s, g.t0, g.coeffs)
+            c.set_stream_start(s, scan.sample0[s])
+            n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
+            c.push(s, np.ascontiguousarray(host_streams[s][: n * scan.G // 4]))
+        c.flush()
+        v, _ = c.correlate()
+        c.close()
+        v = v.reshape(scan.nbl, scan.G, scan.nchan)[:, :nj]
+        err = np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=(1, 2)) / np.sum(np.abs(ref) ** 2, axis=(1, 2)))
+        out[("fp32", "fp16", "fp8")[prec]] = float(err.max())
+    return out
+
+
+def host_stream_prefix(dev_streams, scan, seconds=CPU_SAMPLE_S):
+    spi = int(round(scan.fs * seconds))
     out = []
     for s, t in enumerate(dev_streams):
         n = min(scan.nsamp[s], (spi + 4 * scan.N + 70000) // 16 * 16)
@@ -265,7 +297,7 @@ def run_reference(args):
     rates, secs = [], []
     cores = 1
     for _ in range(args.steps):
-        r, cores, dt, _ = cpu_oracle_sample(scan, streams)
+        r, cores, dt, _, _ = cpu_oracle_sample(scan, streams)
         rates.append(r)
         secs.append(dt)
     value = float(np.mean(rates))
@@ -315,9 +347,8 @@ def dense_leg(args, torch, corr, dev):
     res = {"workload": "cfg3 slice: 64 stations, 16 subbands x 32 MHz, 2 pols, 2-bit, %.2f s of the 4 s scan, "
                        "4096 channels, 0.25 s integrations" % D,
            "station_samples_per_step": sps, "input_bytes": int(sum(int(t.numel()) for t in streams))}
-    for name, prec, bound, measured in (("fp32", corr.CORR_PREC_FP32, 1e-5, "<= 1e-5 (GPU parity tests)"),
-                                        ("fp16", corr.CORR_PREC_FP16_TC, 1.5e-3, "3.1e-4 (64-station parity test)"),
-                                        ("fp8", corr.CORR_PREC_FP8_TC, 8e-2, "3.9e-2 (64-station parity test)")):
+    for name, prec, bound in (("fp32", corr.CORR_PREC_FP32, 1e-5), ("fp16", corr.CORR_PREC_FP16_TC, 1.5e-3),
+                              ("fp8", corr.CORR_PREC_FP8_TC, 8e-2)):
         c = corr.from_scan(sc, device_streams=streams)
         c.set_precision(prec)
         c.set_stream(stream.cuda_stream)
@@ -351,7 +382,7 @@ def dense_leg(args, torch, corr, dev):
         r = {"value": sps / (ms / 1e3), "unit": METRIC, "ms_per_step": ms, "steps": k, "chunk_blocks": cb,
              "fstage_ms_per_step": prof["fstage"][0] / k, "xstep_ms_per_step": x_ms,
              "xstep_tflops": x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None,
-             "error_bound_rel_rms": bound, "measured_rel_rms": measured}
+             "error_bound_rel_rms": bound, "measured_rel_rms": None}
         if prec != corr.CORR_PREC_FP32 and x_ms > 0:
             peak = bf16 * (2.0 if prec == corr.CORR_PREC_FP8_TC else 1.0)
             r["xstep_mma_tflops_issued"] = mma_flops / (x_ms / 1e3) / 1e12
@@ -361,9 +392,12 @@ def dense_leg(args, torch, corr, dev):
     for name in ("fp16", "fp8"):
         if res["fp32"]["xstep_ms_per_step"] > 0:
             res[name]["xstep_vs_fp32_xstep"] = res["fp32"]["xstep_ms_per_step"] / res[name]["xstep_ms_per_step"]
+    # host copy of the scan's first samples, for the measured error of each
+    # precision against the oracle (computed in the CPU-baseline leg)
+    prefix = host_stream_prefix(streams, sc, DENSE_SAMPLE_S)
     del streams
     torch.cuda.empty_cache()
-    return res
+    return res, (sc, prefix)
 
 
 def fringe_leg(args, torch, corr, dev):
@@ -616,13 +650,13 @@ def main():
     roof["issue_frac"] = issue_frac(inst, t_launch, (clocks or {}).get("sm_mhz") or MAX_SM_MHZ)
     launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
-    def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound, measured):
+    def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound):
         xt_ms, xt_n = prof_t["xstage"]
         ft_ms, ft_n = prof_t["fstage"]
         # reduced-precision spectra: elem_bytes read per station-sample in the X step
         xt_bytes = steps * ss_step * elem_bytes
         return {"value": replica_value(sps, ws, ms_t), "unit": METRIC, "ms_per_step": ms_t, "dtype": dtype,
-                "error_bound_rel_rms": bound, "measured_rel_rms": measured,
+                "error_bound_rel_rms": bound, "measured_rel_rms": None,
                 "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
                 "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
                 "xstep_hbm_gbs": xt_bytes / (xt_ms / 1e3) / 1e9 if xt_ms > 0 else None,
@@ -632,11 +666,9 @@ def main():
                 "clocks": clocks_t}
 
     if not args.no_tc:
-        tc = tc_leg(ms_tc, prof_tc, clocks_tc, "f16 in, f32 accumulate", 2.0, 1.5e-3,
-                    "3.0e-4 .. 3.5e-4 (GPU parity tests)")
+        tc = tc_leg(ms_tc, prof_tc, clocks_tc, "f16 in, f32 accumulate", 2.0, 1.5e-3)
     if not args.no_fp8:
-        fp8 = tc_leg(ms_f8, prof_f8, clocks_f8, "e4m3 in, f32 accumulate", 1.0, 8e-2,
-                     "3.8e-2 .. 3.9e-2 (GPU parity tests; 6.3e-2 worst of 2080 baselines at 32 channels)")
+        fp8 = tc_leg(ms_f8, prof_f8, clocks_f8, "e4m3 in, f32 accumulate", 1.0, 8e-2)
 
     # ---- end to end through the host API ----
     # The inputs live in pinned host memory and every step moves them to the
@@ -739,13 +771,14 @@ def main():
     batch = None
     served = None
     dense = None
+    dense_sample = None
     fringe = None
     if rank == 0 and ws == 1:
         # free the single-scan buffers first: the mix brings its own pool
         del out, wts
         torch.cuda.empty_cache()
         if not args.no_dense:
-            dense = dense_leg(args, torch, corr, dev)
+            dense, dense_sample = dense_leg(args, torch, corr, dev)
         if not args.no_fringe:
             fringe = fringe_leg(args, torch, corr, dev)
         if not args.no_batch:
@@ -753,14 +786,32 @@ def main():
         if not args.no_serve:
             served = serve_leg(args, torch, corr, dev)
 
-    # ---- CPU oracle on a bounded sample ----
+    # ---- CPU oracle on a bounded sample; its visibilities also give the
+    #      measured error of every precision on the benchmarked workloads ----
     cpu = None
+    measured = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         hs = host_stream_prefix(dstreams, scan)
-        r, cores, dt, wmin = cpu_oracle_sample(scan, hs)
+        r, cores, dt, wmin, ref = cpu_oracle_sample(scan, hs)
         cpu = {"value": r, "unit": METRIC, "cores": cores, "kind": "oracle",
                "sample": "first %.1f s of the scan as one integration, all stations and streams (%.1f s wall)"
                          % (CPU_SAMPLE_S, dt)}
+        measured = {"sample": "first %.1f s of the benchmarked scan as one integration, all 16 streams; "
+                              "max over the 55 baselines of the relative RMS vs the FP64 oracle" % CPU_SAMPLE_S,
+                    **sample_errors(corr, scan, hs, ref)}
+        if tc is not None:
+            tc["measured_rel_rms"] = measured["fp16"]
+        if fp8 is not None:
+            fp8["measured_rel_rms"] = measured["fp8"]
+        if dense is not None and dense_sample is not None:
+            dsc, dprefix = dense_sample
+            r2, cores2, dt2, _, dref = cpu_oracle_sample(dsc, dprefix, DENSE_SAMPLE_S, DENSE_SAMPLE_STREAMS)
+            derr = sample_errors(corr, dsc, dprefix, dref, DENSE_SAMPLE_S)
+            for name in ("fp32", "fp16", "fp8"):
+                dense[name]["measured_rel_rms"] = derr[name]
+            dense["measured_error_sample"] = ("first %.3f s of the 64-station scan as one integration, streams 0-%d; "
+                                              "max over the 2080 baselines; oracle %.1f s on %d cores"
+                                              % (DENSE_SAMPLE_S, DENSE_SAMPLE_STREAMS - 1, dt2, cores2))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
@@ -773,6 +824,7 @@ def main():
                            "chunk_blocks": cb, "x_partials": kz,
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "measured_rel_rms": measured,
                 "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
                 "dense": dense, "fringe": fringe, "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)

@@ -291,12 +291,19 @@ int corr_fringe_search(const float *dev_vis, int nsub, int nchan, int pad_rate, 
  *
  * The first call on a device resolves the array's device address and loads
  * the FFT constants for that device (no allocation); make that first call
- * before any stream capture.  The work is only enqueued on cuda_stream (NULL:
- * the legacy default stream) when the call returns.  All calls share the one
- * array, which keeps the last call's contents (the partial sums are cleared
- * at the start of every call): calls whose device work overlaps -- on two
- * streams, or from two threads -- race and give wrong results.  Errors are
- * reported by return code only.
+ * before any stream capture.  (After a cudaDeviceReset the next call does
+ * this set-up again for the device's new context.)  Each call copies the
+ * caller's descriptor arrays below from host memory with cudaMemcpyAsync on
+ * cuda_stream, writes the station views and FFT twiddles it derives itself
+ * with small kernels (their values travel as kernel parameters), and only
+ * enqueues the work on cuda_stream (NULL: the legacy default stream) before
+ * it returns.  All calls share the one array, which keeps the last call's
+ * contents (the partial sums and a timeout flag are cleared at the start of
+ * every call): calls whose device work overlaps -- on two streams, or from
+ * two threads -- race and give wrong results.  Errors are reported by return
+ * code only; a device wait of the X step that runs out of time (see
+ * CORR_ETIMEOUT) cannot be reported that way, since the call has returned by
+ * then, so it makes every visibility of the call NaN instead.
  *
  * Descriptor arrays are host memory: nu0_hz[subbands], nseg[stations] (1..64),
  * seg_t0[stations][64], seg_coeffs[stations][64][6] (delay segments as for

@@ -51,9 +51,6 @@ struct Station {
 constexpr int kCopyStreams = 2;             // copies alternate between these
 constexpr size_t kCopyPiece = (size_t)64 << 20;  // large pushes split into pieces
 
-bool g_const_ready[64];
-std::mutex g_const_mu;
-
 }  // namespace
 
 struct corr_s {
@@ -337,13 +334,7 @@ static int prepare(corr_t* h) {
   int rc;
   if ((rc = work_layout(h, w))) return rc;
   h->spi = w.spi;
-  {
-    std::lock_guard<std::mutex> lk(g_const_mu);
-    if (h->dev >= 0 && h->dev < 64 && !g_const_ready[h->dev]) {
-      CK(fstage_init_constants(), "fstage constants");
-      g_const_ready[h->dev] = true;
-    }
-  }
+  CK(fstage_ensure_constants(), "fstage constants");
   const int S = h->S, G = h->G, nch = h->nchan, nbl = nbl_of(S);
   h->Mcap = w.Mcap;
   h->CB = w.CB;
@@ -584,6 +575,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
   fin.wcount = h->d_wcount;
   fin.out = vis_out;
   fin.weights = w_out;
+  fin.err = nullptr;  // the handle reports a device timeout as CORR_ETIMEOUT
   pa = prof_begin(h);
   CK(launch_weights(fin, st), "weights launch");
   if (tc)

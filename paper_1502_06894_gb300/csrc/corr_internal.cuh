@@ -21,6 +21,7 @@ struct StationView {
 };
 
 constexpr int kMaxStations = 256;
+constexpr int kMaxDevices = 64;
 constexpr int kMaxSegs = 64;
 constexpr int kMaxSub = 64;
 
@@ -102,13 +103,19 @@ struct FinParams {
   int* wcount;              // [nbl] scratch
   float2* out;              // [nbl][G][nchan]
   double* weights;          // [nbl] (device, may be null)
+  const int* err;           // optional: when *err != 0 (an X-step wait timed out) the output is NaN
 };
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_delay_blocks(const DelayParams& p, cudaStream_t s);
 cudaError_t launch_unpack_codes(const StationView* st_dev, int station, int G, int j, int64_t t0,
                                 int64_t count, uint8_t* out, cudaStream_t s);
-cudaError_t fstage_init_constants();
+// Load the F kernels' __constant__ tables into the current device's context
+// once (again after a cudaDeviceReset gave the device a new context).
+cudaError_t fstage_ensure_constants();
+// Id of the CUDA context current on this thread (0 when none is bound or
+// the driver cannot say); per-device caches are keyed on it.
+unsigned long long current_context_id();
 bool fstage_supported(int nchan);
 cudaError_t launch_fstage(const FParams& p, cudaStream_t s);
 int xstage_kz(int CB, int S, int G, int nchan);

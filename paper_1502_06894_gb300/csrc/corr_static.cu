@@ -17,7 +17,6 @@
 #include <math.h>
 
 #include <mutex>
-#include <vector>
 
 using namespace corr;
 
@@ -26,33 +25,62 @@ namespace {
 constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // 64 MiB, documented in corr.h
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_ptr[kMaxDevices];  // device address of g_static_scratch per device
+// Device address of g_static_scratch per device, and the context it was
+// resolved in (a cudaDeviceReset gives the device a new context, whose copy
+// of the array may sit elsewhere).
+unsigned char* g_scratch_ptr[kMaxDevices];
+unsigned long long g_scratch_ctx[kMaxDevices];
 std::mutex g_static_mu;
 
 // Errors are reported by return code only (no handle to hold a message).
 int set_err(int code, const char*) { return code; }
 
-// Once per device, with that device current: resolve the array's device
-// address (its host-side name is only a stand-in) and load the FFT constants.
+// Once per device (and context), with that device current: resolve the
+// array's device address (its host-side name is only a stand-in) and load the
+// FFT constants.
 int static_setup(int dev, unsigned char** out) {
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_scratch_ptr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return set_err(CORR_ECUDA, "corr_correlate_static: cudaGetSymbolAddress of the scratch array failed");
     }
-    e = fstage_init_constants();
+    e = fstage_ensure_constants();
     if (e != cudaSuccess) {
       cudaGetLastError();
       return set_err(CORR_ECUDA, "corr_correlate_static: loading FFT constants failed");
     }
     g_scratch_ptr[dev] = (unsigned char*)p;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_ptr[dev];
   return CORR_OK;
+}
+
+// Small inputs that the call derives on the host go to the scratch as kernel
+// parameters (copied at launch), not as copies from host memory that the
+// call frees when it returns: up to kViewsPerLaunch station views per launch,
+// and the FFT twiddles W_N^m = exp(-2 pi i m / N), computed in FP64 on the
+// device and rounded to FP32.
+constexpr int kViewsPerLaunch = 48;
+struct ViewBatch {
+  StationView v[kViewsPerLaunch];
+};
+
+__global__ void k_static_views(ViewBatch b, int n, StationView* dst) {
+  const int i = threadIdx.x;
+  if (i < n) dst[i] = b.v[i];
+}
+
+__global__ void k_static_twiddles(float2* tw, int N) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  double sn, cs;
+  sincospi(-2.0 * (double)m / (double)N, &sn, &cs);
+  tw[m] = make_float2((float)cs, (float)sn);
 }
 
 struct Carve {
@@ -102,6 +130,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
   const size_t o_phi = c.take(sizeof(float) * (size_t)S * nsub * M);
   const size_t o_valid = c.take((size_t)S * M);
   const size_t o_wc = c.take(sizeof(int) * nbl);
+  const size_t o_err = c.take(sizeof(int));
   const size_t fixed = c.off;
   const size_t per_block = sizeof(float2) * (size_t)G * S * nchan;
   const size_t per_part = sizeof(float2) * (size_t)nbl * G * nchan;
@@ -126,33 +155,40 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
-  // ---- host-side copies of the small inputs into the scratch ----
-  std::vector<StationView> views(S);
-  for (int s = 0; s < S; ++s) {
-    views[s].words = (const uint32_t*)d->dev_bytes[s];
-    views[s].nwords = (int64_t)(d->nbytes[s] / 4);
-    views[s].sample0 = d->first_sample[s];
-    views[s].ngroups = (int64_t)((d->nbytes[s] * 4) / (size_t)G);
-    views[s].host = 0;
+  // ---- small inputs into the scratch: the caller's descriptor arrays by
+  //      copies from host memory, the rest by kernels with by-value parameters ----
+  cudaError_t e = cudaSuccess;
+  for (int s0 = 0; s0 < S && e == cudaSuccess; s0 += kViewsPerLaunch) {
+    ViewBatch vb;
+    const int n = (S - s0 < kViewsPerLaunch) ? S - s0 : kViewsPerLaunch;
+    for (int q = 0; q < n; ++q) {
+      const int s = s0 + q;
+      vb.v[q].words = (const uint32_t*)d->dev_bytes[s];
+      vb.v[q].nwords = (int64_t)(d->nbytes[s] / 4);
+      vb.v[q].sample0 = d->first_sample[s];
+      vb.v[q].ngroups = (int64_t)((d->nbytes[s] * 4) / (size_t)G);
+      vb.v[q].host = 0;
+    }
+    k_static_views<<<1, kViewsPerLaunch, 0, st>>>(vb, n, (StationView*)(base + o_views) + s0);
+    e = cudaGetLastError();
   }
-  std::vector<float2> tw(N);
-  for (int m = 0; m < N; ++m) {
-    const double a = -2.0 * 3.14159265358979323846 * (double)m / (double)N;
-    tw[m] = make_float2((float)cos(a), (float)sin(a));
+  if (e == cudaSuccess) {
+    k_static_twiddles<<<(N + 255) / 256, 256, 0, st>>>((float2*)(base + o_tw), N);
+    e = cudaGetLastError();
   }
-  cudaError_t e = cudaMemcpyAsync(base + o_views, views.data(), sizeof(StationView) * S, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_nseg, d->nseg, sizeof(int) * S, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + o_t0, d->seg_t0, sizeof(double) * S * kMaxSegs, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + o_c, d->seg_coeffs, sizeof(double) * S * kMaxSegs * 6, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_nu0, d->nu0_hz, sizeof(double) * nsub, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_tw, tw.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, st);
-  // the X partial sums accumulate, so they must start at zero on every call
+  // the X partial sums accumulate and the timeout flag latches, so both start
+  // at zero on every call
   if (e == cudaSuccess) e = cudaMemsetAsync(base + o_part, 0, per_part * KZ, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, sizeof(int), st);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return set_err(CORR_ECUDA, "corr_correlate_static: copying inputs into the scratch failed");
+    return set_err(CORR_ECUDA, "corr_correlate_static: writing inputs into the scratch failed");
   }
 
   // ---- the same kernels as the handle path ----
@@ -211,7 +247,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     xp.nchan = nchan;
     xp.KZ = KZ;
     xp.part = (float2*)(base + o_part);
-    xp.err = nullptr;
+    xp.err = (int*)(base + o_err);
     e = launch_xstage(xp, st);
   }
   if (e == cudaSuccess) {
@@ -228,6 +264,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     fin.wcount = (int*)(base + o_wc);
     fin.out = (float2*)dev_out;
     fin.weights = dev_weights;
+    fin.err = (const int*)(base + o_err);  // a timed-out X-step wait turns the output into NaN
     e = launch_weights(fin, st);
     if (e == cudaSuccess) e = launch_finalize(fin, st);
   }

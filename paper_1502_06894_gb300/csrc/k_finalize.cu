@@ -41,6 +41,7 @@ __global__ void k_finalize(FinParams p) {
   const size_t per = (size_t)p.G * p.nchan;
   const size_t total = (size_t)nbl_of(p.S) * per;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const bool failed = p.err && *p.err != 0;
   for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
     const int bl = (int)(e / per);
     float2 v = make_float2(0.f, 0.f);
@@ -51,7 +52,8 @@ __global__ void k_finalize(FinParams p) {
     }
     const int w = p.wcount[bl];
     const float sc = w > 0 ? (float)(1.0 / ((double)w * (double)p.N)) : 0.f;
-    p.out[e] = make_float2(v.x * sc, v.y * sc);
+    p.out[e] = failed ? make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000))
+                      : make_float2(v.x * sc, v.y * sc);
   }
 }
 

@@ -24,10 +24,13 @@
 // delay segment yet) store zeros, so they add nothing in the X step.
 #include "corr_internal.cuh"
 
+#include <cuda.h>
 #include <cuda_fp8.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <math.h>
+#include <mutex>
 
 namespace corr {
 
@@ -39,13 +42,58 @@ __device__ __forceinline__ uint32_t fp8x2(float re, float im) {
 
 __constant__ float2 c_w32[32];  // exp(-2 pi i m / 32)
 
-cudaError_t fstage_init_constants() {
+static cudaError_t fstage_init_constants() {
   float2 h[32];
   for (int m = 0; m < 32; ++m) {
     double a = -2.0 * 3.14159265358979323846 * (double)m / 32.0;
     h[m] = make_float2((float)cos(a), (float)sin(a));
   }
   return cudaMemcpyToSymbol(c_w32, h, sizeof(h));
+}
+
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+namespace {
+std::mutex g_const_mu;
+unsigned long long g_const_ctx[kMaxDevices];  // context the constants were loaded into, per device
+}  // namespace
+
+cudaError_t fstage_ensure_constants() {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  // a host-side lookup that also binds the device's context and loads this
+  // module, so that the context id below is the one the kernels run in
+  void* sym = nullptr;
+  if ((e = cudaGetSymbolAddress(&sym, c_w32)) != cudaSuccess) return e;
+  const unsigned long long id = current_context_id();
+  std::lock_guard<std::mutex> lk(g_const_mu);
+  // id 0 (no context id available): load once per device
+  if (g_const_ctx[dev] != 0 && (id == 0 || g_const_ctx[dev] == id)) return cudaSuccess;
+  if ((e = fstage_init_constants()) != cudaSuccess) return e;
+  g_const_ctx[dev] = id ? id : ~0ull;
+  return cudaSuccess;
 }
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }

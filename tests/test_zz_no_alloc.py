@@ -8,7 +8,8 @@ so that pytest collects it last.  The test calls the entry point twice in a
 row through the C ABI and checks each result against the handle path
 (corr_correlate_device) on the same device-resident samples, with the same
 tolerance the other parity tests use (1e-5 relative RMS per baseline, weights
-exact).  It must pass alone in a fresh process and after the other tests.
+exact); then it checks that further calls leave the device's free memory
+unchanged.  It must pass alone in a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -55,6 +56,19 @@ def test_static_scratch_matches_handle_path_twice():
         assert st.correlate(i, out[i], w[i]) == corr.CORR_OK
     torch.cuda.synchronize()
     c.close()
+    torch.cuda.synchronize()
+
+    # the property the entry point exists for: once the first calls have run
+    # (module and kernels loaded), further calls take no device memory
+    again = torch.empty_like(out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        for i in range(2):
+            assert st.correlate(i, again[i]) == corr.CORR_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(again, out)  # the same inputs give the same result, call after call
 
     R, O = ref.cpu().numpy(), out.cpu().numpy()
     assert np.array_equal(w.cpu().numpy(), wref.cpu().numpy())
