@@ -184,7 +184,9 @@ int corr_next_integration(const corr_t *h, int64_t *index);
 int corr_rewind(corr_t *h);
 
 /* Drop all pushed or attached samples and flush state, and rewind; the delay
- * model, format and stream starts are kept. */
+ * model, format and stream starts are kept.  Also clears a device timeout
+ * (CORR_ETIMEOUT) that a correlate call reported, so the handle can be used
+ * again. */
 int corr_reset(corr_t *h);
 
 /* Text of the last error on h (NULL h: last corr_create failure). */
@@ -230,6 +232,17 @@ int corr_debug_codes(corr_t *h, int station, int stream, int64_t t0, int64_t cou
 /* The rotated spectrum of one station, stream and block (nchan complex64),
  * as the F step produces it; *valid receives the block's validity. */
 int corr_debug_spectrum(corr_t *h, int station, int stream, int64_t block, float *out, int *valid);
+
+/* Spins (polls of an mbarrier) before a device wait of the X kernels gives
+ * up, for every launch after the call, process-wide; negative restores the
+ * default (2^26, far beyond any wait a working kernel needs); 0 makes every
+ * such wait give up at once.  A test hook for the timeout path: a kernel
+ * whose wait gives up stops its work, waits (with the default bound) for the
+ * bulk copies and tensor-core operations it has in flight, frees its tensor
+ * memory and sets an error flag, which a handle reports as CORR_ETIMEOUT
+ * (corr_correlate / the next call) and corr_correlate_static as NaN
+ * visibilities.  The visibilities of such a call are not meaningful. */
+int corr_debug_set_wait_limit(long long spins);
 
 /* Time every stage launch with CUDA events on the handle's stream (off by
  * default).  Stages: 0 delay blocks, 1 F (unpack+FFT+rotate), 2 X

@@ -75,6 +75,7 @@ _SIGS = {
     "corr_debug_delays": ([_H, C.c_int64, C.c_int64, _P, _P, _P, _P], C.c_int),
     "corr_debug_codes": ([_H, C.c_int, C.c_int, C.c_int64, C.c_int64, _P], C.c_int),
     "corr_debug_spectrum": ([_H, C.c_int, C.c_int, C.c_int64, _P, C.POINTER(C.c_int)], C.c_int),
+    "corr_debug_set_wait_limit": ([C.c_longlong], C.c_int),
     "corr_set_profiling": ([_H, C.c_int], C.c_int),
     "corr_read_profile": ([_H, _P, _P], C.c_int),
     "corr_launch_shape": ([_H, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),

@@ -999,6 +999,13 @@ int corr_reset(corr_t* h) {
   }
   h->flushed = false;
   h->next_int = 0;
+  // a device wait that timed out earlier no longer blocks the handle
+  if (h->prepared) {
+    cudaError_t e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "corr_reset: error flag");
+    *h->h_err = 0;
+  }
   return CORR_OK;
 }
 
@@ -1180,6 +1187,11 @@ int corr_launch_shape(const corr_t* h, int* chunk_blocks, int* kz) {
   if (!h || !chunk_blocks || !kz) return CORR_EINVAL;
   *chunk_blocks = h->CB;
   *kz = h->KZ;
+  return CORR_OK;
+}
+
+int corr_debug_set_wait_limit(long long spins) {
+  set_wait_limit(spins);
   return CORR_OK;
 }
 

@@ -84,6 +84,7 @@ struct XTC2Params {
   int fp8;                  // tiles hold E4M3 values (MMA kind::f8f6f4) instead of FP16 (kind::f16)
   float2* part;             // [G][nchan][nbl]
   int* err;
+  long long wait_limit;     // spins per mbarrier wait (set by the launcher)
 };
 
 // X stage: V_ab[k] += X_a[k] conj(X_b[k]) over the chunk's blocks.
@@ -93,6 +94,7 @@ struct XParams {
   int KZ;                   // block splits per chunk (one partial each)
   float2* part;             // [KZ][nbl][G][nchan]
   int* err;                 // set to 1 when a device wait times out (may be null)
+  long long wait_limit;     // spins per mbarrier wait (set by the launcher)
 };
 
 struct FinParams {
@@ -123,6 +125,10 @@ cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
 cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, cudaStream_t s);
 int xtc_cpt(int S);
+// Spins before a device wait of the X kernels gives up (negative: the
+// default); process-wide, read at every launch.  A test hook.
+void set_wait_limit(long long spins);
+long long wait_limit();
 bool fstage_tc_tiles_supported(int nchan);
 cudaError_t launch_fstage_tc(const FParams& p, const TcTiles& o, cudaStream_t s);
 cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s);

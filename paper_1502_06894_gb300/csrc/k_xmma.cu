@@ -19,10 +19,13 @@
 // partial sums in global memory.  Both element types advance 32 bytes of a
 // row per MMA, so the shared-memory descriptors are the same.
 // Every wait on an mbarrier is bounded; on timeout the CTA sets *err, stops
-// issuing work, waits for its own copies, frees its TMEM and returns.
+// issuing work, waits (again bounded) for the bulk copies and MMAs it has in
+// flight, frees its TMEM and returns.
 #include "corr_internal.cuh"
 
 #include <cuda_fp16.h>
+
+#include <atomic>
 
 namespace corr {
 
@@ -30,7 +33,8 @@ namespace {
 
 constexpr int kKT = 64;            // blocks per K tile (64 FP16 = one 128-byte swizzle row)
 constexpr int kTileBytes = 128 * kKT * 2;  // one 128-row operand tile
-constexpr long kWaitLimit = 1L << 26;      // spins before an mbarrier wait gives up
+constexpr long long kWaitLimit = 1LL << 26;  // spins before an mbarrier wait gives up (default)
+constexpr long long kDrainLimit = 1LL << 26; // spins per wait while draining after an abort
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -97,9 +101,10 @@ namespace {
 constexpr int kStages2 = 6;
 constexpr int kPairBytes = 2 * kTileBytes;  // two channel-group tiles per K tile
 
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                                long long limit) {
   uint32_t ok = 0;
-  for (long it = 0; it < kWaitLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
         : "=r"(ok)
@@ -107,6 +112,21 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, 
         : "memory");
     if (ok) return true;
     if ((it & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+// A bounded wait that ignores the abort flag: used after an abort, for the
+// CTA's own copies and MMAs, which finish by themselves.
+__device__ __forceinline__ bool mbar_drain_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok = 0;
+  for (long long it = 0; it < kDrainLimit; ++it) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
   }
   return false;
 }
@@ -129,7 +149,7 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* ring = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // [kStages2][32 KB]
-  __shared__ __align__(8) uint64_t s_full[kStages2], s_empty[kStages2], s_acc_full[2], s_acc_empty[2];
+  __shared__ __align__(8) uint64_t s_full[kStages2], s_empty[kStages2], s_acc_full[2], s_acc_empty[2], s_drain;
   __shared__ uint32_t s_taddr;
   __shared__ volatile int s_abort;
 
@@ -147,6 +167,7 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_acc_full[i])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(smem_u32(&s_acc_empty[i])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_drain)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
@@ -165,6 +186,10 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
 
   if (warp == 4) {
     if (lane == 0) {
+      const long long lim = p.wait_limit;
+      int loaded = 0;  // tiles whose bulk copy has been issued
+      int landed = 0;  // tiles whose copy has been seen complete
+      bool mma_issued = false;
       auto load = [&](int u) {
         const int n = u / NKT, kt = u - n * NKT;
         const int item = blockIdx.x + n * gridDim.x;  // = g * nslice + sl
@@ -178,14 +203,16 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
                 smem_u32(ring + st * kPairBytes)),
             "l"(src), "r"(kPairBytes), "r"(smem_u32(&s_full[st]))
             : "memory");
+        loaded = u + 1;
       };
       for (int u = 0; u < kStages2 && u < my_tiles; ++u) load(u);
       for (int u = 0; u < my_tiles && !s_abort; ++u) {
         const int n = u / NKT, kt = u - n * NKT;
         const int st = u % kStages2;
         const int ab = n & 1;
-        if (!mbar_wait_abort(&s_full[st], (u / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
-        if (kt == 0 && n >= 2 && !mbar_wait_abort(&s_acc_empty[ab], ((n - 2) >> 1) & 1, &s_abort)) {
+        if (!mbar_wait_abort(&s_full[st], (u / kStages2) & 1, &s_abort, lim)) { s_abort = 1; break; }
+        landed = u + 1;
+        if (kt == 0 && n >= 2 && !mbar_wait_abort(&s_acc_empty[ab], ((n - 2) >> 1) & 1, &s_abort, lim)) {
           s_abort = 1;
           break;
         }
@@ -202,6 +229,7 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
               mma_f16(taddr + ab * 256 + grp * 128, d0 + 2ull * ks, d0 + 2ull * ks, (kt > 0 || ks > 0) ? 1u : 0u);
           }
         }
+        mma_issued = true;
         mma_commit(&s_empty[st]);
         if (kt == NKT - 1) mma_commit(&s_acc_full[ab]);
         // refill the stage of the previous tile (its MMAs have had a whole
@@ -210,9 +238,20 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
           const int pv = u - 1;
           const int nxt = pv + kStages2;
           if (nxt < my_tiles) {
-            if (!mbar_wait_abort(&s_empty[pv % kStages2], (pv / kStages2) & 1, &s_abort)) { s_abort = 1; break; }
+            if (!mbar_wait_abort(&s_empty[pv % kStages2], (pv / kStages2) & 1, &s_abort, lim)) { s_abort = 1; break; }
             load(nxt);
           }
+        }
+      }
+      if (s_abort) {
+        // drain before the CTA's shared memory and TMEM go away: every bulk
+        // copy issued lands (each tile's full barrier completes its phase),
+        // and every MMA issued completes (a commit of all prior tcgen05
+        // operations of this thread to a barrier of its own)
+        for (int t = landed; t < loaded; ++t) mbar_drain_wait(&s_full[t % kStages2], (t / kStages2) & 1);
+        if (mma_issued) {
+          mma_commit(&s_drain);
+          mbar_drain_wait(&s_drain, 0);
         }
       }
     }
@@ -233,7 +272,7 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
     const int q0 = (2 * S * cmin) / 32, q1 = (warp * 32 < rows_valid) ? (2 * S * (cmax + 1) - 1) / 32 : -1;
     for (int n = 0; n < my_items; ++n) {
       const int ab = n & 1;
-      const bool timed_out = !mbar_wait_abort(&s_acc_full[ab], (n >> 1) & 1, &s_abort);
+      const bool timed_out = !mbar_wait_abort(&s_acc_full[ab], (n >> 1) & 1, &s_abort, p.wait_limit);
       // the four epilogue warps share named barriers below, so they stop
       // together: a barrier OR over their timeouts and the abort flag
       if (bar_or_128(timed_out || s_abort)) {
@@ -295,7 +334,16 @@ __global__ void __launch_bounds__(160, 1) k_xmma2(XTC2Params p, int nitems) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(taddr));
 }
 
-cudaError_t launch_xtc2(const XTC2Params& p, int sm_count, cudaStream_t s) {
+namespace {
+std::atomic<long long> g_wait_limit{kWaitLimit};
+}
+
+void set_wait_limit(long long spins) { g_wait_limit.store(spins < 0 ? kWaitLimit : spins); }
+long long wait_limit() { return g_wait_limit.load(); }
+
+cudaError_t launch_xtc2(const XTC2Params& p_in, int sm_count, cudaStream_t s) {
+  XTC2Params p = p_in;
+  p.wait_limit = wait_limit();
   const int nitems = p.G * p.nslice;
   if (nitems <= 0 || p.NKT <= 0) return cudaSuccess;
   // the bulk-copy ring plus the epilogue's stage of W * nbl complex values

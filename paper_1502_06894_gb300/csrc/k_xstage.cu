@@ -203,7 +203,7 @@ __host__ __device__ constexpr int tri_split(int TA, int npart, int part) {
   return i;
 }
 
-constexpr long kXWaitLimit = 1L << 26;
+constexpr long long kXDrainLimit = 1LL << 26;  // spins per wait while draining after an abort
 
 __device__ __forceinline__ uint32_t xs_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
 
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
       if (tid == 0) issue(q + kStagesX - 1);  // the slot of stage q-1, freed by the sync below
       const int slot = q % kStagesX;
       uint32_t ok = 0;
-      for (long it = 0; it < kXWaitLimit && !ok; ++it) {
+      for (long long it = 0; it < p.wait_limit && !ok; ++it) {
         asm volatile(
             "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
             : "=r"(ok)
@@ -300,12 +300,13 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
       __syncthreads();
     }
     if (s_abort) {
-      // let the copies already issued land before the CTA's shared memory goes away
+      // let the copies already issued land before the CTA's shared memory
+      // goes away: stage q (whose wait gave up) and the ones issued after it
       if (tid == 0) {
-        for (int r = q + 1; r < q + kStagesX && r < nst; ++r) {
+        for (int r = q; r < q + kStagesX && r < nst; ++r) {
           const int slot = r % kStagesX;
           uint32_t ok = 0;
-          for (long it = 0; it < kXWaitLimit && !ok; ++it)
+          for (long long it = 0; it < kXDrainLimit && !ok; ++it)
             asm volatile(
                 "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
                 : "=r"(ok)
@@ -354,8 +355,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 template <int TA>
-static cudaError_t launch_tma(const XParams& p, cudaStream_t s, bool* used) {
+static cudaError_t launch_tma(const XParams& p_in, cudaStream_t s, bool* used) {
   *used = false;
+  XParams p = p_in;
+  p.wait_limit = wait_limit();
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc || p.nchan < kXT || kNB * p.S > 256) return cudaSuccess;
   CUtensorMap tm;
