@@ -39,7 +39,11 @@ class _Scan(C.Structure):
         ("nu0", C.c_void_p), ("nseg", C.c_void_p), ("seg_t0", C.c_void_p), ("seg_c", C.c_void_p),
         ("maxseg", C.c_int),
         ("bytes", C.c_void_p), ("byte_off", C.c_void_p), ("sample0", C.c_void_p), ("nsamp", C.c_void_p),
+        ("rotation", C.c_int),
     ]
+
+ROT_POST_F = 0   # fringe rotation after the transform, at the block centre (the default)
+ROT_PRE_F = 1    # per-sample fringe rotation before a complex transform
 
 
 def lib():
@@ -49,6 +53,7 @@ def lib():
         L = C.CDLL(_LIB)
         P = C.c_void_p
         L.oracle_delays.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P]
+        L.oracle_delays_ex.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P, P]
         L.oracle_correlate_ex.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
         L.oracle_correlate_ex.restype = C.c_int
         L.oracle_spectrum.argtypes = [P, C.c_int, C.c_int, C.c_int64, P]
@@ -74,7 +79,7 @@ class Oracle:
 
     def __init__(self, stations: int, nsub: int, npol: int, nchan: int, fs: float, tint: float,
                  nu0: Sequence[float], polys, streams: Sequence[np.ndarray],
-                 sample0: Sequence[int], nsamp: Sequence[int], lut=DEFAULT_LUT):
+                 sample0: Sequence[int], nsamp: Sequence[int], lut=DEFAULT_LUT, rotation: int = ROT_POST_F):
         S = stations
         self.S, self.nsub, self.npol, self.nchan = S, nsub, npol, nchan
         self.G = nsub * npol
@@ -101,25 +106,28 @@ class Oracle:
         self._lens = [len(b) for b in streams]
         self._sc = _Scan(S, nsub, npol, nchan, self.fs, self.tint, (C.c_double * 4)(*lut),
                          _ptr(self._nu0), _ptr(self._nseg), _ptr(self._t0), _ptr(self._c), maxseg,
-                         _ptr(self._bytes), _ptr(self._off), _ptr(self._s0), _ptr(self._ns))
+                         _ptr(self._bytes), _ptr(self._off), _ptr(self._s0), _ptr(self._ns), int(rotation))
 
     @classmethod
-    def from_scan(cls, scan, streams, lut=DEFAULT_LUT, nsamp=None):
+    def from_scan(cls, scan, streams, lut=DEFAULT_LUT, nsamp=None, rotation=ROT_POST_F):
         return cls(scan.stations, scan.nsub, scan.npol, scan.nchan, scan.fs, scan.tint, scan.nu0,
-                   scan.polys, streams, scan.sample0, nsamp if nsamp is not None else scan.nsamp, lut)
+                   scan.polys, streams, scan.sample0, nsamp if nsamp is not None else scan.nsamp, lut,
+                   rotation)
 
     @property
     def nbl(self) -> int:
         return self.S * (self.S + 1) // 2
 
-    def delays(self, b0: int, nb: int):
-        """(n_b, eps, tau, valid), each [S, nb]."""
+    def delays(self, b0: int, nb: int, rate: bool = False):
+        """(n_b, eps, tau, valid), each [S, nb]; with rate=True also the delay
+        rate d tau/dt at each block centre."""
         n = np.zeros((self.S, nb), np.int64)
         e = np.zeros((self.S, nb))
         t = np.zeros((self.S, nb))
         v = np.zeros((self.S, nb), np.uint8)
-        lib().oracle_delays(C.byref(self._sc), b0, nb, _ptr(n), _ptr(e), _ptr(t), _ptr(v))
-        return n, e, t, v
+        r = np.zeros((self.S, nb))
+        lib().oracle_delays_ex(C.byref(self._sc), b0, nb, _ptr(n), _ptr(e), _ptr(t), _ptr(v), _ptr(r))
+        return (n, e, t, v, r) if rate else (n, e, t, v)
 
     def _check_bytes(self):
         for s, n in enumerate(self._lens):

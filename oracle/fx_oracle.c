@@ -29,8 +29,14 @@
  *             SPI = fs*tint samples per integration (an integer).
  *   spectrum  X[k] = sum_n x[n] exp(-2 pi i k n / N), k = 0..N/2-1 (DC kept,
  *             Nyquist dropped), unnormalised, rectangular window.
- *   rotation  post-F at the block centre: X[k] *= exp(+2 pi i (phi + f_k eps)),
- *             phi = frac(nu0 * tau), f_k = k*fs/N.
+ *   rotation  post-F (the default) at the block centre:
+ *             X[k] *= exp(+2 pi i (phi + f_k eps)), phi = frac(nu0 * tau), f_k = k*fs/N.
+ *             pre-F (selectable): the fringe phase is applied per sample before
+ *             the transform, linear about the block centre,
+ *               y[n] = x[n] exp(+2 pi i (phi + nu0 tau'(t_c) (n - N/2) / fs)),
+ *             tau' the derivative of the delay polynomial at t_c; then the
+ *             complex N-point transform Y[k] = sum_n y[n] exp(-2 pi i k n / N),
+ *             k = 0..N/2-1, and the fractional-delay slope Y[k] *= exp(+2 pi i f_k eps).
  *   X-step    V_ab[k] = sum over blocks of X_a[k] conj(X_b[k]) for a <= b,
  *             parallel hands only; baselines (0,0),(0,1),..,(1,1),..
  *   output    V_ab / (W_ab * N); zero where W_ab = 0.
@@ -64,6 +70,7 @@ typedef struct {
   const int64_t *byte_off;/* [S] offset of each station's bytes             */
   const int64_t *sample0; /* [S] station sample index of the first group    */
   const int64_t *nsamp;   /* [S] number of sample-time groups present       */
+  int rotation;           /* 0: post-F fringe rotation, 1: pre-F            */
 } oracle_scan;
 
 /* ------------------------------------------------------------------------ */
@@ -86,6 +93,7 @@ void oracle_unpack_codes(const uint8_t *bytes, int G, int j, int64_t t0, int64_t
 typedef struct {
   int64_t nstart;  /* n_b: integer-sample delay                            */
   double tau;      /* delay at the block centre (s)                        */
+  double rate;     /* d tau / dt at the block centre (s/s)                 */
   double eps;      /* tau - n_b/fs (s)                                     */
   int covered;     /* t_c lies at or after the first segment's t0          */
 } oracle_delay;
@@ -106,6 +114,10 @@ static oracle_delay block_delay(const oracle_scan *sc, int s, int64_t b) {
   double tau = c[5];
   for (int i = 4; i >= 0; --i) tau = fma(tau, u, c[i]);
   d.tau = tau;
+  /* derivative of the same polynomial, sum_{i>=1} i c_i u^(i-1) */
+  double rate = 0.0;
+  for (int i = 5; i >= 1; --i) rate = rate * u + (double)i * c[i];
+  d.rate = rate;
   d.nstart = (int64_t)floor(fma(tau, sc->fs, 0.5));
   d.eps = tau - (double)d.nstart / sc->fs;
   return d;
@@ -117,9 +129,10 @@ static int block_valid(const oracle_scan *sc, int s, int64_t b, const oracle_del
   return d->covered && i0 >= sc->sample0[s] && i0 + N <= sc->sample0[s] + sc->nsamp[s];
 }
 
-/* Per (station, block): n_b, eps, tau and validity for blocks [b0, b0+nb). */
-void oracle_delays(const oracle_scan *sc, int64_t b0, int64_t nb,
-                   int64_t *nstart, double *eps, double *tau, uint8_t *valid) {
+/* Per (station, block): n_b, eps, tau, validity and (if rate != NULL) the
+ * delay rate for blocks [b0, b0+nb). */
+void oracle_delays_ex(const oracle_scan *sc, int64_t b0, int64_t nb, int64_t *nstart, double *eps,
+                      double *tau, uint8_t *valid, double *rate) {
   for (int s = 0; s < sc->S; ++s)
     for (int64_t i = 0; i < nb; ++i) {
       oracle_delay d = block_delay(sc, s, b0 + i);
@@ -128,7 +141,14 @@ void oracle_delays(const oracle_scan *sc, int64_t b0, int64_t nb,
       eps[o] = d.eps;
       tau[o] = d.tau;
       valid[o] = (uint8_t)block_valid(sc, s, b0 + i, &d);
+      if (rate) rate[o] = d.rate;
     }
+}
+
+/* Per (station, block): n_b, eps, tau and validity for blocks [b0, b0+nb). */
+void oracle_delays(const oracle_scan *sc, int64_t b0, int64_t nb,
+                   int64_t *nstart, double *eps, double *tau, uint8_t *valid) {
+  oracle_delays_ex(sc, b0, nb, nstart, eps, tau, valid, NULL);
 }
 
 /* Absolute fringe phase in turns, frac(nu0 * tau), in FP64. */
@@ -184,12 +204,32 @@ static int station_spectrum(const oracle_scan *sc, int s, int j, int64_t b,
   }
   const uint8_t *bytes = sc->bytes + sc->byte_off[s];
   int64_t t0 = b * (int64_t)N + d.nstart - sc->sample0[s];
+  double nu0 = sc->nu0[j / sc->npol];
+  double phi = fringe_turns(nu0, d.tau);
+  if (sc->rotation == 1) {
+    /* pre-F: per-sample fringe phase, linear about the block centre */
+    double per_sample = nu0 * d.rate / sc->fs;
+    for (int n = 0; n < N; ++n) {
+      double a = 2.0 * ORACLE_PI * (phi + per_sample * (double)(n - N / 2));
+      double x = sc->lut[oracle_code(bytes, G, t0 + n, j)];
+      re[n] = x * cos(a);
+      im[n] = x * sin(a);
+    }
+    oracle_fft(re, im, N, 0);
+    for (int k = 0; k < sc->nchan; ++k) {
+      double fk = (double)k * sc->fs / (double)N;
+      double a = 2.0 * ORACLE_PI * fk * d.eps;
+      double c = cos(a), sn = sin(a);
+      xr[k] = re[k] * c - im[k] * sn;
+      xi[k] = re[k] * sn + im[k] * c;
+    }
+    return 1;
+  }
   for (int n = 0; n < N; ++n) {
     re[n] = sc->lut[oracle_code(bytes, G, t0 + n, j)];
     im[n] = 0.0;
   }
   oracle_fft(re, im, N, 0);
-  double phi = fringe_turns(sc->nu0[j / sc->npol], d.tau);
   for (int k = 0; k < sc->nchan; ++k) {
     double fk = (double)k * sc->fs / (double)N;
     double a = 2.0 * ORACLE_PI * (phi + fk * d.eps);
