@@ -56,6 +56,8 @@ def lib():
         L.oracle_delays_ex.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P, P]
         L.oracle_correlate_ex.argtypes = [P, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_int, P, P]
         L.oracle_correlate_ex.restype = C.c_int
+        L.oracle_correlate_cross.argtypes = [P, C.c_int64, C.c_int, P, P]
+        L.oracle_correlate_cross.restype = C.c_int
         L.oracle_spectrum.argtypes = [P, C.c_int, C.c_int, C.c_int64, P]
         L.oracle_spectrum.restype = C.c_int
         L.oracle_fft.argtypes = [P, P, C.c_int, C.c_int]
@@ -142,6 +144,20 @@ class Oracle:
         vis = np.zeros((ni, nbl, nj, self.nchan, 2))
         w = np.zeros((ni, nbl))
         rc = lib().oracle_correlate_ex(C.byref(self._sc), i0, ni, j0, nj, int(full), _ptr(vis), _ptr(w))
+        if rc != 0:
+            raise ValueError("oracle: fs*tint must be a whole number of samples")
+        return vis[..., 0] + 1j * vis[..., 1], w
+
+    def correlate_cross(self, i0: int = 0, ni: int = 1):
+        """Both hands of two polarisations: visibilities [ni, nbl, nsub, 4, nchan]
+        complex128 (hand products pq = 00, 01, 10, 11: X_a^p conj(X_b^q)) and
+        weights [ni, nbl]."""
+        self._check_bytes()
+        if self.npol != 2:
+            raise ValueError("cross-hand products need two polarisations")
+        vis = np.zeros((ni, self.nbl, self.nsub, 4, self.nchan, 2))
+        w = np.zeros((ni, self.nbl))
+        rc = lib().oracle_correlate_cross(C.byref(self._sc), i0, ni, _ptr(vis), _ptr(w))
         if rc != 0:
             raise ValueError("oracle: fs*tint must be a whole number of samples")
         return vis[..., 0] + 1j * vis[..., 1], w

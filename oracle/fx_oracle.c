@@ -38,7 +38,10 @@
  *             complex N-point transform Y[k] = sum_n y[n] exp(-2 pi i k n / N),
  *             k = 0..N/2-1, and the fractional-delay slope Y[k] *= exp(+2 pi i f_k eps).
  *   X-step    V_ab[k] = sum over blocks of X_a[k] conj(X_b[k]) for a <= b,
- *             parallel hands only; baselines (0,0),(0,1),..,(1,1),..
+ *             parallel hands (stream by stream); baselines (0,0),(0,1),..,(1,1),..
+ *             With both hands of two polarisations (selectable, npol = 2):
+ *             V_ab^pq[k] = sum over blocks of X_a^p[k] conj(X_b^q[k]) for every
+ *             a <= b and p, q in {0, 1}, hand products ordered pq = 00, 01, 10, 11.
  *   output    V_ab / (W_ab * N); zero where W_ab = 0.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC (the FP64 delay
@@ -321,6 +324,74 @@ int oracle_correlate_ex(const oracle_scan *sc, int64_t i0, int ni, int j0, int n
 int oracle_correlate(const oracle_scan *sc, int64_t i0, int ni, int j0, int nj,
                      double *vis, double *weights) {
   return oracle_correlate_ex(sc, i0, ni, j0, nj, 0, vis, weights);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Both hands of two polarisations, for integrations [i0, i0+ni):           */
+/* vis [ni][nbl][nsub][4][nchan][2], hand product pq = 2p + q, i.e.         */
+/* V_ab^pq = sum over blocks of X_a^p conj(X_b^q); weights [ni][nbl].       */
+
+int oracle_correlate_cross(const oracle_scan *sc, int64_t i0, int ni, double *vis, double *weights) {
+  const int S = sc->S, N = 2 * sc->nchan, nch = sc->nchan, nsub = sc->nsub;
+  const int nbl = S * (S + 1) / 2;
+  if (sc->npol != 2) return -2;
+  int64_t spi = llround(sc->fs * sc->tint);
+  if (fabs(sc->fs * sc->tint - (double)spi) > 1e-6 || spi <= 0) return -1;
+  memset(vis, 0, sizeof(double) * 2 * (size_t)ni * nbl * nsub * 4 * nch);
+  if (weights) memset(weights, 0, sizeof(double) * (size_t)ni * nbl);
+
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int sb = 0; sb < nsub; ++sb) {
+    double *re = malloc(sizeof(double) * N), *im = malloc(sizeof(double) * N);
+    /* spectra of both pols of every station: [p][s][k] */
+    double *xr = malloc(sizeof(double) * 2 * (size_t)S * nch), *xi = malloc(sizeof(double) * 2 * (size_t)S * nch);
+    double *acc = malloc(sizeof(double) * 2 * (size_t)nbl * 4 * nch);
+    int *ok = malloc(sizeof(int) * S);
+    for (int ii = 0; ii < ni; ++ii) {
+      int64_t bfirst = integ_first_block(i0 + ii, spi, N);
+      int64_t bend = integ_first_block(i0 + ii + 1, spi, N);
+      memset(acc, 0, sizeof(double) * 2 * (size_t)nbl * 4 * nch);
+      double *w = malloc(sizeof(double) * nbl);
+      memset(w, 0, sizeof(double) * nbl);
+      for (int64_t b = bfirst; b < bend; ++b) {
+        for (int p = 0; p < 2; ++p)
+          for (int s = 0; s < S; ++s) {
+            size_t o = ((size_t)p * S + s) * nch;
+            /* validity depends on the station and block only */
+            ok[s] = station_spectrum(sc, s, sb * 2 + p, b, re, im, xr + o, xi + o);
+          }
+        int bl = 0;
+        for (int a = 0; a < S; ++a)
+          for (int c = a; c < S; ++c, ++bl) {
+            if (!(ok[a] && ok[c])) continue;
+            w[bl] += 1.0;
+            for (int p = 0; p < 2; ++p)
+              for (int q = 0; q < 2; ++q) {
+                const double *ar = xr + ((size_t)p * S + a) * nch, *ai = xi + ((size_t)p * S + a) * nch;
+                const double *cr = xr + ((size_t)q * S + c) * nch, *ci = xi + ((size_t)q * S + c) * nch;
+                double *o = acc + 2 * ((size_t)bl * 4 + 2 * p + q) * nch;
+                for (int k = 0; k < nch; ++k) {
+                  /* X_a^p conj(X_c^q) */
+                  o[2 * k] += ar[k] * cr[k] + ai[k] * ci[k];
+                  o[2 * k + 1] += ai[k] * cr[k] - ar[k] * ci[k];
+                }
+              }
+          }
+      }
+      for (int bl = 0; bl < nbl; ++bl) {
+        double scale = w[bl] > 0 ? 1.0 / (w[bl] * (double)N) : 0.0;
+        for (int pq = 0; pq < 4; ++pq) {
+          double *dst = vis + 2 * (((((size_t)ii * nbl + bl) * nsub + sb) * 4 + pq) * nch);
+          const double *src = acc + 2 * ((size_t)bl * 4 + pq) * nch;
+          for (int k = 0; k < 2 * nch; ++k) dst[k] = src[k] * scale;
+        }
+        if (weights && sb == 0) weights[(size_t)ii * nbl + bl] = w[bl];
+      }
+      free(w);
+    }
+    free(re); free(im); free(xr); free(xi); free(acc); free(ok);
+  }
+  return 0;
 }
 
 int oracle_threads(void) {
