@@ -68,6 +68,14 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense 64-station X-step leg")
     ap.add_argument("--dense-duration", type=float, default=0.5,
                     help="seconds of the 64-station scan in the dense leg (the named scan is 4 s)")
+    ap.add_argument("--dense-tint", type=float, default=0.25,
+                    help="integration time of the dense leg (0.25 s is the workload; shorter only for profiling)")
+    ap.add_argument("--dense-chunk-blocks", type=int, default=0,
+                    help="FFT blocks per chunk in the dense leg (0: library default; smaller only for profiling)")
+    ap.add_argument("--dense-stations", type=int, default=64,
+                    help="stations of the dense leg (64 is the workload; fewer only for profiling its F kernel)")
+    ap.add_argument("--dense-only", action="store_true",
+                    help="run only the dense 64-station leg and print its result (for profiling)")
     ap.add_argument("--no-fringe", action="store_true", help="skip the delay-rate fringe-search leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 96-scan batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the served leg")
@@ -322,8 +330,8 @@ def dense_leg(args, torch, corr, dev):
     algorithmic work) against the measured dense BF16 peak (x2 for FP8)."""
     import synth
     D = args.dense_duration
-    sc = synth.config2(seed=3, duration=D, tint=0.25, boundary=D / 2, nchan=4096, stations=64, nsub=16, npol=2,
-                       fs=64e6, nu0_base=1.6e9)
+    sc = synth.config2(seed=3, duration=D, tint=args.dense_tint, boundary=D / 2, nchan=4096,
+                       stations=args.dense_stations, nsub=16, npol=2, fs=64e6, nu0_base=1.6e9)
     gen = torch.Generator(device=dev)
     gen.manual_seed(3003)
     streams = [device_codes(sc.nsamp[s] * sc.G // 4, gen, dev) for s in range(sc.stations)]
@@ -351,6 +359,8 @@ def dense_leg(args, torch, corr, dev):
                               ("fp8", corr.CORR_PREC_FP8_TC, 8e-2)):
         c = corr.from_scan(sc, device_streams=streams)
         c.set_precision(prec)
+        if args.dense_chunk_blocks:
+            c.set_chunk_blocks(args.dense_chunk_blocks)
         c.set_stream(stream.cuda_stream)
         c.flush()
 
@@ -533,6 +543,11 @@ def main():
     _build.build()
     from paper_1502_06894_gb300 import corr
 
+    if args.dense_only:
+        res, _ = dense_leg(args, torch, corr, dev)
+        print(json.dumps({"dense": res}), flush=True)
+        return
+
     scan = make_scan(args.seed + rank, args.duration)
     nint = int(round(scan.duration / scan.tint))
     gen = torch.Generator(device=dev)
@@ -552,12 +567,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def device_leg(precision):
+    def device_leg(precision, pipeline=1):
         """Time K steps of the device-resident path at one precision."""
         c = corr.from_scan(scan, device_streams=dstreams)
         if args.chunk_blocks:
             c.set_chunk_blocks(args.chunk_blocks)
         c.set_precision(precision)
+        c.set_pipeline(pipeline)
         c.set_stream(stream.cuda_stream)
         c.flush()
 
@@ -591,9 +607,13 @@ def main():
         ms = max_over_ranks(ms, dev)
         return ms, prof, clocks, shape
 
-    ms, prof, clocks, (cb, kz) = device_leg(corr.CORR_PREC_FP32)
+    ms, prof_ovl, clocks, (cb, kz) = device_leg(corr.CORR_PREC_FP32)
     sps = samples_per_step(scan)
     value = replica_value(sps, ws, ms)
+    # the same step with F and X in turn on one stream: each kernel's launch
+    # time then is its own (with the overlap, F launches share SMs with X), so
+    # this leg gives the per-kernel roofline
+    ms_seq, prof, clocks_seq, _ = device_leg(corr.CORR_PREC_FP32, pipeline=0)
     tc = None
     if not args.no_tc:
         ms_tc, prof_tc, clocks_tc, _ = device_leg(corr.CORR_PREC_FP16_TC)
@@ -648,7 +668,7 @@ def main():
     inst = profile_value("instructions.txt", kname)
     roof["warp_instructions"] = inst
     roof["issue_frac"] = issue_frac(inst, t_launch, (clocks or {}).get("sm_mhz") or MAX_SM_MHZ)
-    launches = prof["delay"][1] + prof["fstage"][1] + prof["xstage"][1] + 2 * prof["finalize"][1]
+    launches = prof_ovl["delay"][1] + prof_ovl["fstage"][1] + prof_ovl["xstage"][1] + 2 * prof_ovl["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
     def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound):
         xt_ms, xt_n = prof_t["xstage"]
@@ -825,7 +845,15 @@ def main():
                            "parallelism": "replicas x%d" % ws},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "measured_rel_rms": measured,
-                "clocks": clocks, "stages": stages, "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
+                "clocks": clocks, "stages": stages,
+                "schedule": {"value": "two streams: X of chunk c overlaps F of chunk c+1, delay blocks one "
+                                      "integration ahead",
+                             "roofline_and_stages": "F and X in turn on one stream (each launch timed alone)",
+                             "sequential_ms_per_step": ms_seq,
+                             "overlapped_stages": {k: {"ms_per_step": v[0] / args.steps,
+                                                       "launches_per_step": v[1] / args.steps}
+                                                   for k, v in prof_ovl.items()}},
+                "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
                 "dense": dense, "fringe": fringe, "batch": batch, "serve": served}
         print(json.dumps(line), flush=True)
     if ws > 1:

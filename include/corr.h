@@ -102,10 +102,54 @@ int corr_set_sky_freq(corr_t *h, int subband, double nu0_hz);
  * correlate call (CORR_ESTATE). */
 int corr_set_precision(corr_t *h, int mode);
 
+/* Where the fringe rotation is applied.  CORR_ROT_POST_F (the default): after
+ * the transform, one phase frac(nu0 tau(t_c)) per block and channel slope, as
+ * in step 4 above.  CORR_ROT_PRE_F: before the transform, every sample x[n] of
+ * a block is multiplied by exp(+2 pi i (frac(nu0 tau(t_c)) + nu0 tau'(t_c)
+ * (n - N/2) / fs)) -- the fringe phase linear about the block centre, tau'
+ * the delay polynomial's derivative, phase and rate from the FP64 delay model
+ * and FP32 increments within the block -- then a complex N-point transform
+ * keeps channels 0..nchan-1 and applies exp(+2 pi i k fs/N eps).  At a
+ * spacecraft's delay rate the fringe phase turns several times within one
+ * block (the paper, Sec. 2: the delay model follows RadioAstron's large and
+ * fast-changing velocity; at 4.8 GHz and 3e-5 s/s, 9 turns in a 64 us block);
+ * post-F rotation then loses the fringe to that drift (|sinc(turns per
+ * block)|) while pre-F keeps it.  The lowest channels receive the image of
+ * the negative frequencies shifted by twice the fringe rate.  Pre-F takes
+ * nchan <= 4096 (CORR_EINVAL otherwise) and about twice the F-step work.
+ * Only before the first correlate call (CORR_ESTATE). */
+enum { CORR_ROT_POST_F = 0, CORR_ROT_PRE_F = 1 };
+int corr_set_fringe_rotation(corr_t *h, int mode);
+
+/* Which polarisation products the X step forms.  CORR_POL_PARALLEL (the
+ * default): each polarisation with itself, V_ab^pp, output
+ * [baseline][subband][pol][channel].  CORR_POL_CROSS (pols = 2 only): all
+ * four hand products V_ab^pq[k] = sum over blocks of X_a^p[k] conj(X_b^q[k]),
+ * p, q in {0, 1} (for circular feeds RR, RL, LR, LL), output
+ * [baseline][subband][pq = 2p + q][channel] -- twice the output of the
+ * parallel hands, so the out buffers of corr_correlate* hold
+ * nbl * subbands * 4 * nchan complex values.  The polarisation key science
+ * programmes that the paper's AO-1 correlation serves (Sec. 1) need them.
+ * The X step runs over 2S (station, pol) pairs per subband, about twice the
+ * parallel hands' work; the tensor-core modes then take at most 32 stations.
+ * Only before the first correlate call (CORR_ESTATE). */
+enum { CORR_POL_PARALLEL = 0, CORR_POL_CROSS = 1 };
+int corr_set_pol_products(corr_t *h, int mode);
+
 /* FFT blocks per F/X chunk (0, the default: as many as fit 1 GiB of FP32
  * spectra, capped at one integration).  Smaller chunks keep the spectra in
  * L2 between the F and X kernels.  Only before the first correlate call. */
 int corr_set_chunk_blocks(corr_t *h, int blocks);
+
+/* Schedule of the F and X steps.  1 (the default): two spectra (or
+ * tensor-core tile) buffers, and the X step of each chunk runs on a second,
+ * higher-priority stream while the F step of the next chunk runs, whenever
+ * one buffer takes at most 4 GiB; 0: one buffer, F and X in turn.  Either
+ * way the next integration's delay blocks are evaluated on a side stream
+ * during the current one.  The results are the same; 1 is faster and holds
+ * the spectra twice (corr_device_bytes tells).  Only before the first
+ * correlate call. */
+int corr_set_pipeline(corr_t *h, int overlap);
 
 /* Run device work on this cudaStream_t (NULL: the handle's own stream). */
 int corr_set_stream(corr_t *h, void *cuda_stream);
@@ -338,6 +382,56 @@ typedef struct {
 
 int corr_correlate_static(const corr_scan_desc *desc, int64_t integration, float *dev_out,
                           double *dev_weights, void *cuda_stream);
+
+/* ---- continuous-batching server -------------------------------------------
+ *
+ * A correlation service for many scans of uneven shape (the workloads a
+ * correlator centre such as the paper's, Sec. 1, runs one after another).
+ * corr_server_start starts one worker thread on the device current at the
+ * call.  Jobs submitted from any thread wait in a first-come-first-served
+ * queue; the worker admits them while the device memory they need (the
+ * handle's work buffers, corr_device_bytes, plus their output buffers) fits
+ * hbm_cap_bytes - reserve_bytes, so jobs that arrive while others are on the
+ * GPU join as memory frees up.  Every step advances every admitted job by
+ * one integration in one CUDA graph (corr_batch_run) and calls each job's
+ * callback, on the worker thread, with that integration's visibilities
+ * (host memory, [nbl][subbands][pols][nchan] complex64, the corr_correlate
+ * layout) and weights (nbl doubles), valid only during the call.  A job's
+ * result does not depend on the other jobs in the mix (each keeps its own
+ * work buffers and accumulation order).
+ *
+ * A job is a corr_scan_desc (shapes, format, delay model; the stations'
+ * samples in device memory of the server's device, which the caller keeps
+ * alive and unchanged until the job's last callback), the X-step precision
+ * (CORR_PREC_*), the fringe-rotation form (CORR_ROT_*) and the number of
+ * integrations to correlate from integration 0.  The descriptor arrays are
+ * copied at submission.  A job that cannot fit even alone, or whose handle
+ * cannot be made, gets one callback with vis = weights = NULL and status
+ * CORR_ENOMEM or the handle's error code; so does every job still queued or
+ * running at corr_server_stop (status CORR_ESTATE).
+ *
+ * corr_server_stats: median and 99th-percentile latency (nearest rank,
+ * seconds from submission to the end of the last callback) over finished
+ * jobs, station-samples per second from the first submission to the last
+ * finish, and the number of finished jobs (any pointer may be NULL).
+ * corr_server_wait blocks until every submitted job has finished
+ * (timeout_s < 0: no limit; CORR_ETIMEOUT when the limit passes first).
+ * corr_server_stop finishes the step in progress, fails what is left and
+ * joins the worker. */
+typedef struct corr_server_s corr_server_t;
+typedef struct {
+  corr_scan_desc scan;
+  int precision;
+  int rotation;
+  int64_t integrations;
+} corr_job;
+typedef void (*corr_result_fn)(void *user, int64_t job_id, int64_t integration, const float *vis,
+                               const double *weights, int status);
+int corr_server_start(corr_server_t **srv, size_t hbm_cap_bytes, size_t reserve_bytes);
+int corr_server_submit(corr_server_t *srv, const corr_job *job, corr_result_fn fn, void *user, int64_t *job_id);
+int corr_server_stats(corr_server_t *srv, double *p50_s, double *p99_s, double *samples_per_s, int64_t *jobs_done);
+int corr_server_wait(corr_server_t *srv, double timeout_s);
+void corr_server_stop(corr_server_t *srv);
 
 #ifdef __cplusplus
 }

@@ -16,9 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libcorr.so")
-SOURCES = ["corr_capi.cu", "k_delay.cu", "k_fstage.cu", "k_xstage.cu", "k_finalize.cu", "k_xmma.cu", "corr_static.cu",
-           "k_fringe.cu"]
-HEADERS = ["corr_internal.cuh"]
+SOURCES = ["corr_capi.cu", "k_delay.cu", "k_fstage.cu", "k_fstage_pre.cu", "k_xstage.cu", "k_finalize.cu", "k_xmma.cu",
+           "corr_static.cu", "k_fringe.cu", "corr_server.cu"]
+HEADERS = ["corr_internal.cuh", "k_fstage_impl.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

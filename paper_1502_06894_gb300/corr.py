@@ -28,6 +28,10 @@ CORR_ETOOBIG = -8
 CORR_PREC_FP32 = 0
 CORR_PREC_FP16_TC = 1
 CORR_PREC_FP8_TC = 2
+CORR_ROT_POST_F = 0
+CORR_ROT_PRE_F = 1
+CORR_POL_PARALLEL = 0
+CORR_POL_CROSS = 1
 
 _ERRNAMES = {0: "CORR_OK", -1: "CORR_EINVAL", -2: "CORR_ENOMEM", -3: "CORR_EAGAIN", -4: "CORR_ETIMEOUT",
              -5: "CORR_ECUDA", -6: "CORR_ESTATE", -7: "CORR_EEND", -8: "CORR_ETOOBIG"}
@@ -47,6 +51,14 @@ class CorrScanDesc(C.Structure):
                 ("seg_coeffs", C.c_void_p), ("dev_bytes", C.c_void_p), ("nbytes", C.c_void_p),
                 ("first_sample", C.c_void_p)]
 
+class CorrJob(C.Structure):
+    """corr_job of include/corr.h."""
+    _fields_ = [("scan", CorrScanDesc), ("precision", C.c_int), ("rotation", C.c_int), ("integrations", C.c_int64)]
+
+
+RESULT_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int64, C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_double),
+                        C.c_int)
+
 _P = C.c_void_p
 _H = C.c_void_p
 _SIGS = {
@@ -56,6 +68,9 @@ _SIGS = {
     "corr_set_precision": ([_H, C.c_int], C.c_int),
     "corr_set_stream": ([_H, _P], C.c_int),
     "corr_set_chunk_blocks": ([_H, C.c_int], C.c_int),
+    "corr_set_pipeline": ([_H, C.c_int], C.c_int),
+    "corr_set_fringe_rotation": ([_H, C.c_int], C.c_int),
+    "corr_set_pol_products": ([_H, C.c_int], C.c_int),
     "corr_set_delay_poly": ([_H, C.c_int, C.c_double, _P], C.c_int),
     "corr_set_stream_start": ([_H, C.c_int, C.c_int64], C.c_int),
     "corr_reserve": ([_H, C.c_int, C.c_size_t], C.c_int),
@@ -82,6 +97,12 @@ _SIGS = {
     "corr_correlate_static": ([C.POINTER(CorrScanDesc), C.c_int64, _P, _P, _P], C.c_int),
     "corr_batch_run": ([_P, C.c_int, _P, _P, _P], C.c_int),
     "corr_device_bytes": ([_H, C.POINTER(C.c_size_t)], C.c_int),
+    "corr_server_start": ([C.POINTER(_H), C.c_size_t, C.c_size_t], C.c_int),
+    "corr_server_submit": ([_H, C.POINTER(CorrJob), RESULT_FN, _P, C.POINTER(C.c_int64)], C.c_int),
+    "corr_server_stats": ([_H, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                           C.POINTER(C.c_int64)], C.c_int),
+    "corr_server_wait": ([_H, C.c_double], C.c_int),
+    "corr_server_stop": ([_H], None),
     "corr_fringe_search": ([_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, C.POINTER(C.c_int), C.POINTER(C.c_int),
                             C.POINTER(C.c_float), _P, _P], C.c_int),
 }
@@ -158,6 +179,16 @@ class Correlator:
     def set_precision(self, mode: int):
         self._check(corr_set_precision(self.h, int(mode)))
 
+    def set_fringe_rotation(self, mode: int):
+        self._check(corr_set_fringe_rotation(self.h, int(mode)))
+
+    def set_pol_products(self, mode: int):
+        self._check(corr_set_pol_products(self.h, int(mode)))
+        self.cross = mode == CORR_POL_CROSS
+
+    def set_pipeline(self, overlap: int):
+        self._check(corr_set_pipeline(self.h, int(overlap)))
+
     def set_chunk_blocks(self, blocks: int):
         self._check(corr_set_chunk_blocks(self.h, int(blocks)))
 
@@ -224,8 +255,10 @@ class Correlator:
     # ---------------------------------------------------------------- run
     def correlate(self, weights: bool = True):
         """Next integration -> (vis [nbl, nsub, npol, nchan] complex64, weights [nbl])
-        or None when the library answers CORR_EAGAIN / CORR_EEND."""
-        out = np.empty((self.nbl, self.nsub, self.npol, self.nchan), np.complex64)
+        or None when the library answers CORR_EAGAIN / CORR_EEND.  With both
+        hands (set_pol_products(CORR_POL_CROSS)) vis is [nbl, nsub, 4, nchan]."""
+        out = np.empty((self.nbl, self.nsub, 4 if getattr(self, "cross", False) else self.npol, self.nchan),
+                       np.complex64)
         w = np.empty(self.nbl, np.float64) if weights else None
         rc = corr_correlate(self.h, _ptr(out), _ptr(w))
         if rc in (CORR_EAGAIN, CORR_EEND):
@@ -376,3 +409,74 @@ def fringe_search(vis, pad_rate: int, pad_delay: int, stream: Optional[int] = No
     if rc != CORR_OK:
         raise CorrError(rc, "corr_fringe_search")
     return out, (r.value, l.value, a.value, complex(val[0], val[1]))
+
+
+class Server:
+    """The continuous-batching server of libcorr (corr_server_*): a worker
+    thread admits submitted jobs by device memory and advances all admitted
+    jobs one integration per CUDA graph.  ``on_result(job_id, integration,
+    vis, weights, status)`` runs on that worker thread; vis (complex64
+    [nbl, nsub, npol, nchan]) and weights are copies."""
+
+    def __init__(self, hbm_cap: int, reserve: int, on_result=None):
+        h = _H()
+        rc = corr_server_start(C.byref(h), int(hbm_cap), int(reserve))
+        if rc != CORR_OK:
+            raise CorrError(rc, "corr_server_start")
+        self.h = h
+        self.on_result = on_result
+        self._jobs = {}   # key (the callback's user pointer) -> job metadata
+        self._next_key = 1
+
+        def trampoline(user, job_id, integration, vis, weights, status):
+            meta = self._jobs.get(user or 0)
+            v = w = None
+            if status == CORR_OK and meta is not None:
+                nbl, nsub, npol, nchan = meta["shape"]
+                v = np.ctypeslib.as_array(vis, shape=(nbl * nsub * npol * nchan * 2,)).view(np.complex64).reshape(
+                    nbl, nsub, npol, nchan).copy()
+                w = np.ctypeslib.as_array(weights, shape=(nbl,)).copy()
+            if meta is not None and (status != CORR_OK or integration + 1 >= meta["nint"]):
+                self._jobs.pop(user, None)
+            if self.on_result is not None:
+                self.on_result(job_id, integration, v, w, status)
+
+        self._cb = RESULT_FN(trampoline)
+
+    def submit(self, static_scan: "StaticScan", integrations: int, precision: int = CORR_PREC_FP32,
+               rotation: int = CORR_ROT_POST_F) -> int:
+        """Queue a job: the scan held by a StaticScan (samples in device
+        memory, which must stay alive until the job's last result)."""
+        job = CorrJob(static_scan.desc, int(precision), int(rotation), int(integrations))
+        jid = C.c_int64()
+        d = static_scan.desc
+        nbl = d.stations * (d.stations + 1) // 2
+        key = self._next_key
+        self._next_key += 1
+        # registered before the worker can report on it
+        self._jobs[key] = {"shape": (nbl, d.subbands, d.pols, d.nchan), "nint": int(integrations),
+                           "keep": static_scan}
+        rc = corr_server_submit(self.h, C.byref(job), self._cb, C.c_void_p(key), C.byref(jid))
+        if rc != CORR_OK:
+            self._jobs.pop(key, None)
+            raise CorrError(rc, "corr_server_submit")
+        return jid.value
+
+    def stats(self):
+        p50, p99, sps, n = C.c_double(), C.c_double(), C.c_double(), C.c_int64()
+        corr_server_stats(self.h, C.byref(p50), C.byref(p99), C.byref(sps), C.byref(n))
+        return {"p50_s": p50.value, "p99_s": p99.value, "station_samples_per_s": sps.value, "jobs_done": n.value}
+
+    def wait(self, timeout: float = -1.0) -> int:
+        return corr_server_wait(self.h, float(timeout))
+
+    def close(self):
+        if getattr(self, "h", None):
+            corr_server_stop(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

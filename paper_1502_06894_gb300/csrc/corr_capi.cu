@@ -61,6 +61,8 @@ struct corr_s {
   float lut[4] = {-3.336f, -1.0f, 1.0f, 3.336f};
   std::vector<double> nu0;
   int precision = CORR_PREC_FP32;
+  int rotation = CORR_ROT_POST_F;
+  int pol_products = CORR_POL_PARALLEL;
   cudaStream_t own_stream = nullptr;
   cudaStream_t copy_stream[kCopyStreams] = {nullptr, nullptr};
   int copy_next = 0;
@@ -80,15 +82,31 @@ struct corr_s {
   double* d_seg_c = nullptr;
   double* d_nu0 = nullptr;
   int Mcap = 0;
-  int64_t* d_start = nullptr;
-  float* d_delta = nullptr;
-  float* d_phi = nullptr;
-  uint8_t* d_valid = nullptr;
-  unsigned long long* d_stat = nullptr;  // [S][3]
-  unsigned long long* h_stat = nullptr;  // pinned
+  // Block descriptors, double-buffered: integration i uses slot i & 1, so the
+  // next integration's delay blocks are evaluated (on dstream) while this
+  // one's F and X steps run.
+  int64_t* d_start[2] = {};
+  float* d_delta[2] = {};
+  float* d_phi[2] = {};
+  float2* d_dphi[2] = {};  // pre-F: phase step per sample (hi, lo), [S][nsub][Mcap]
+  uint8_t* d_valid[2] = {};
+  unsigned long long* d_stat[2] = {};  // [S][3] data-coverage statistics
+  unsigned long long* h_stat[2] = {};  // pinned copies
+  unsigned long long* h_stat_init = nullptr;  // pinned, the statistics' start values
   float2* d_twN = nullptr;
   int CB = 0, KZ = 0;
-  float2* d_spec = nullptr;
+  // spectra chunk (and tensor-core tiles): two buffers when the F step of
+  // chunk c+1 runs while the X step of chunk c does (on xstream)
+  float2* d_spec[2] = {};
+  bool overlap = false;
+  int pipeline = 1;  // corr_set_pipeline: 1 overlap F and X when the buffers allow, 0 never
+  cudaStream_t xstream = nullptr;  // X step, higher priority
+  cudaStream_t dstream = nullptr;  // look-ahead delay blocks
+  cudaEvent_t ev_f[2] = {}, ev_x[2] = {}, ev_main = nullptr, ev_la = nullptr;
+  bool x_pending[2] = {false, false};
+  bool la_valid = false;           // integration la_int's delay blocks are (being) evaluated
+  int64_t la_int = -1;
+  uint64_t model_gen = 1, la_gen = 0;  // bumped whenever the delay model or station data change
   float2* d_part = nullptr;
   float2* d_out = nullptr;
   int* d_wcount = nullptr;
@@ -99,7 +117,7 @@ struct corr_s {
   int sigma = 0;      // FP16 / FP8 spectra carry X * 2^-sigma
   int* d_err = nullptr;
   int* h_err = nullptr;  // pinned
-  unsigned char* d_tiles = nullptr;  // tensor-core operand tiles (FFT length <= 2048)
+  unsigned char* d_tiles[2] = {};  // tensor-core operand tiles
   bool tc_tiles = false;
   bool tc_direct = false;  // the F step writes the tiles itself
 
@@ -135,6 +153,16 @@ struct corr_s {
 
 static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
+// The X step's view of the spectra: with both hands of two polarisations it
+// runs over 2S virtual stations (station, pol) and nsub streams.
+static bool cross_of(const corr_t* h) { return h->pol_products == CORR_POL_CROSS; }
+static int x_stations(const corr_t* h) { return cross_of(h) ? 2 * h->S : h->S; }
+static int x_streams(const corr_t* h) { return cross_of(h) ? h->nsub : h->G; }
+// complex values per baseline in the output: [subband][pol or hand product][channel]
+static size_t out_per_baseline(const corr_t* h) {
+  return (size_t)h->nsub * (cross_of(h) ? 4 : h->npol) * h->nchan;
+}
+
 static int use_device(corr_t* h) {
   int cur = -1;
   cudaGetDevice(&cur);
@@ -160,22 +188,32 @@ static cudaEvent_t take_event(corr_t* h) {
 }
 
 // Record an event before (begin) / after (end) a stage's launch when profiling.
-static cudaEvent_t prof_begin(corr_t* h) {
+static cudaEvent_t prof_begin(corr_t* h, cudaStream_t st) {
   if (!h->profiling) return nullptr;
   cudaEvent_t a = take_event(h);
-  if (a) cudaEventRecord(a, h->stream);
+  if (a) cudaEventRecord(a, st);
   return a;
 }
 
-static void prof_end(corr_t* h, int stage, cudaEvent_t a) {
+static void prof_end(corr_t* h, int stage, cudaEvent_t a, cudaStream_t st) {
   if (!a) return;
   cudaEvent_t b = take_event(h);
   if (!b) {
     h->ev_pool.push_back(a);
     return;
   }
-  cudaEventRecord(b, h->stream);
+  cudaEventRecord(b, st);
   h->marks.push_back({stage, a, b});
+}
+
+// Wait for a look-ahead delay evaluation in flight and forget it.
+static int drop_lookahead(corr_t* h) {
+  if (h->dstream) {
+    cudaError_t e = cudaStreamSynchronize(h->dstream);
+    if (e != cudaSuccess) return h->cuda_fail(e, "look-ahead delay blocks");
+  }
+  h->la_valid = false;
+  return CORR_OK;
 }
 
 static int prof_collect(corr_t* h) {
@@ -220,14 +258,30 @@ static void free_device(corr_t* h) {
   cudaFree(h->d_seg_t0);
   cudaFree(h->d_seg_c);
   cudaFree(h->d_nu0);
-  cudaFree(h->d_start);
-  cudaFree(h->d_delta);
-  cudaFree(h->d_phi);
-  cudaFree(h->d_valid);
-  cudaFree(h->d_stat);
-  cudaFreeHost(h->h_stat);
+  for (int q = 0; q < 2; ++q) {
+    cudaFree(h->d_start[q]);
+    cudaFree(h->d_delta[q]);
+    cudaFree(h->d_phi[q]);
+    cudaFree(h->d_dphi[q]);
+    cudaFree(h->d_valid[q]);
+    cudaFree(h->d_stat[q]);
+    cudaFreeHost(h->h_stat[q]);
+    cudaFree(h->d_spec[q]);
+    cudaFree(h->d_tiles[q]);
+    h->d_start[q] = nullptr; h->d_delta[q] = nullptr; h->d_phi[q] = nullptr; h->d_dphi[q] = nullptr;
+    h->d_valid[q] = nullptr; h->d_stat[q] = nullptr; h->h_stat[q] = nullptr; h->d_spec[q] = nullptr;
+    h->d_tiles[q] = nullptr;
+    if (h->ev_f[q]) cudaEventDestroy(h->ev_f[q]);
+    if (h->ev_x[q]) cudaEventDestroy(h->ev_x[q]);
+    h->ev_f[q] = h->ev_x[q] = nullptr;
+    h->x_pending[q] = false;
+  }
+  if (h->ev_main) cudaEventDestroy(h->ev_main);
+  if (h->ev_la) cudaEventDestroy(h->ev_la);
+  h->ev_main = h->ev_la = nullptr;
+  cudaFreeHost(h->h_stat_init);
+  h->h_stat_init = nullptr;
   cudaFree(h->d_twN);
-  cudaFree(h->d_spec);
   cudaFree(h->d_part);
   cudaFree(h->d_out);
   cudaFree(h->d_wcount);
@@ -235,17 +289,15 @@ static void free_device(corr_t* h) {
   h->d_wts = nullptr;
   cudaFree(h->d_err);
   cudaFreeHost(h->h_err);
-  cudaFree(h->d_tiles);
-  h->d_tiles = nullptr;
   h->d_err = nullptr;
   h->h_err = nullptr;
   h->d_views = nullptr; h->h_views = nullptr; h->d_nseg = nullptr; h->d_seg_t0 = nullptr;
-  h->d_seg_c = nullptr; h->d_nu0 = nullptr; h->d_start = nullptr; h->d_delta = nullptr;
-  h->d_phi = nullptr; h->d_valid = nullptr; h->d_stat = nullptr; h->h_stat = nullptr;
-  h->d_twN = nullptr; h->d_spec = nullptr; h->d_part = nullptr; h->d_out = nullptr;
+  h->d_seg_c = nullptr; h->d_nu0 = nullptr;
+  h->d_twN = nullptr; h->d_part = nullptr; h->d_out = nullptr;
   h->d_wcount = nullptr;
   h->prepared = false;
   h->views_valid = false;
+  h->la_valid = false;
 }
 
 static int dalloc(corr_t* h, void** p, size_t bytes, const char* what) {
@@ -263,9 +315,14 @@ struct WorkLayout {
   int64_t spi = 0;
   int Mcap = 0, CB = 0, KZ = 0;
   bool tiles = false, direct = false;
-  size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;
-  size_t total() const { return spec + part + tiles_bytes + small; }
+  int nbuf = 1;  // spectra / tile buffers: 2 when F and X overlap
+  size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;  // spec, tiles_bytes: per buffer
+  size_t total() const { return nbuf * (spec + tiles_bytes) + part + small; }
 };
+
+// F and X overlap (two spectra / tile buffers) unless one buffer is already
+// this large: the dense many-station shapes, which the F step dominates.
+constexpr size_t kOverlapMaxBuffer = (size_t)4 << 30;
 
 static int work_layout(corr_t* h, WorkLayout& w) {
   const double spi = h->fs * h->tint;
@@ -273,12 +330,16 @@ static int work_layout(corr_t* h, WorkLayout& w) {
     return h->fail(CORR_EINVAL, "fs*tint = %.9g must be a whole number of samples >= 2*nchan", spi);
   w.spi = llround(spi);
   const int S = h->S, G = h->G, nch = h->nchan;
+  const int XS = x_stations(h), XG = x_streams(h);
   const size_t nbl = (size_t)nbl_of(S);
   w.Mcap = (int)((w.spi + h->N - 1) / h->N) + 1;
   const size_t per_block = (size_t)G * S * nch * sizeof(float2);
   const bool tc = h->precision != CORR_PREC_FP32;
   const bool fp8 = h->precision == CORR_PREC_FP8_TC;
   const int kb = fp8 ? 128 : 64;  // blocks per K tile
+  // the F step writes tensor-core tiles itself for FFTs of up to 2048 points
+  // and post-F rotation; otherwise FP16 / FP8 spectra are corner-turned
+  const bool direct_ok = fstage_tc_tiles_supported(nch) && h->rotation == CORR_ROT_POST_F && !cross_of(h);
   int64_t cb = h->chunk_req > 0 ? h->chunk_req : (int64_t)(h->spec_budget / per_block);
   if (h->chunk_req <= 0) {
     // Every chunk reads and writes all partial visibilities once; chunks of at
@@ -290,13 +351,12 @@ static int work_layout(corr_t* h, WorkLayout& w) {
     // plus FP16 / FP8 spectra when a corner turn builds the tiles) against
     // sixteen times the budget, since at many stations every accumulator
     // read-out costs as much as several K tiles.
-    const int64_t want = tc ? std::max<int64_t>(8 * (int64_t)(S + 1), 512) : 4 * (int64_t)(S + 1);
+    const int64_t want = tc ? std::max<int64_t>(8 * (int64_t)(XS + 1), 512) : 4 * (int64_t)(XS + 1);
     int64_t cap = (int64_t)(4 * h->spec_budget / per_block);
-    if (tc && xtc_cpt(S) > 0) {
-      const int W = 2 * xtc_cpt(S);
-      const size_t tiles_per_block = (size_t)G * ((nch + W - 1) / W) * 32768 / kb;
-      const size_t tc_per_block =
-          tiles_per_block + (fstage_tc_tiles_supported(nch) ? 0 : per_block / (fp8 ? 4 : 2));
+    if (tc && xtc_cpt(XS) > 0) {
+      const int W = 2 * xtc_cpt(XS);
+      const size_t tiles_per_block = (size_t)XG * ((nch + W - 1) / W) * 32768 / kb;
+      const size_t tc_per_block = tiles_per_block + (direct_ok ? 0 : per_block / (fp8 ? 4 : 2));
       cap = std::max<int64_t>(cap, (int64_t)(16 * h->spec_budget / tc_per_block));
     }
     if (cb < want) cb = std::min(want, std::max(cap, cb));
@@ -307,24 +367,29 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   // no zero padding except in the last chunk of an integration
   if (tc && h->chunk_req <= 0 && cb > kb) cb -= cb % kb;
   w.CB = (int)cb;
-  w.KZ = xstage_kz(w.CB, S, G, nch);
+  w.KZ = xstage_kz(w.CB, XS, XG, nch);
   // tensor-core operand tiles hold up to 64 stations; for FFTs of up to 2048
   // points the F step writes them directly, above that FP16 (FP8) spectra are
   // corner-turned into them
-  w.tiles = tc && xtc_cpt(S) > 0;
-  w.direct = w.tiles && fstage_tc_tiles_supported(nch);
+  w.tiles = tc && xtc_cpt(XS) > 0;
+  w.direct = w.tiles && direct_ok;
   w.spec = w.direct ? 16 : (w.tiles ? per_block / (fp8 ? 4 : 2) * w.CB : per_block * w.CB);
   // partial sums: KZ slices for the FP32 X step, one for the tensor cores
-  w.part = sizeof(float2) * (size_t)(tc ? 1 : w.KZ) * nbl * G * nch;
+  w.part = sizeof(float2) * (size_t)(tc ? 1 : w.KZ) * nbl_of(XS) * XG * nch;
   if (w.tiles) {
-    const int W = 2 * xtc_cpt(S);
-    w.tiles_bytes = (size_t)G * ((nch + W - 1) / W) * ((size_t)(w.CB + kb - 1) / kb) * 32768;
+    const int W = 2 * xtc_cpt(XS);
+    w.tiles_bytes = (size_t)XG * ((nch + W - 1) / W) * ((size_t)(w.CB + kb - 1) / kb) * 32768;
   }
+  w.nbuf = (h->pipeline && w.spec + w.tiles_bytes <= kOverlapMaxBuffer) ? 2 : 1;
   const size_t M = (size_t)w.Mcap;
+  // descriptors (two slots), model, twiddles, output, weights
   w.small = sizeof(StationView) * S + sizeof(int) * S + sizeof(double) * S * kMaxSegs * 7 +
-            sizeof(double) * h->nsub + (sizeof(int64_t) + sizeof(float) + 1) * S * M +
-            sizeof(float) * S * h->nsub * M + sizeof(unsigned long long) * 3 * S + sizeof(float2) * h->N +
-            sizeof(float2) * nbl * G * nch + (sizeof(int) + sizeof(double)) * nbl + sizeof(int);
+            sizeof(double) * h->nsub +
+            2 * ((sizeof(int64_t) + sizeof(float) + 1) * S * M + sizeof(float) * S * h->nsub * M +
+                 sizeof(unsigned long long) * 3 * S +
+                 (h->rotation == CORR_ROT_PRE_F ? sizeof(float2) * S * h->nsub * M : 0)) +
+            sizeof(float2) * h->N + sizeof(float2) * nbl * out_per_baseline(h) + (sizeof(int) + sizeof(double)) * nbl +
+            sizeof(int);
   return CORR_OK;
 }
 
@@ -354,16 +419,35 @@ static int prepare(corr_t* h) {
   if ((rc = dalloc(h, (void**)&h->d_seg_t0, sizeof(double) * S * kMaxSegs, "seg_t0"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_seg_c, sizeof(double) * S * kMaxSegs * 6, "seg_c"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_nu0, sizeof(double) * h->nsub, "nu0"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_start, sizeof(int64_t) * S * h->Mcap, "start"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_delta, sizeof(float) * S * h->Mcap, "delta"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_phi, sizeof(float) * S * h->nsub * h->Mcap, "phi"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_valid, (size_t)S * h->Mcap, "valid"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_stat, sizeof(unsigned long long) * 3 * S, "stat"))) return rc;
-  CK(cudaMallocHost((void**)&h->h_stat, sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
+  for (int q = 0; q < 2; ++q) {
+    if ((rc = dalloc(h, (void**)&h->d_start[q], sizeof(int64_t) * S * h->Mcap, "start"))) return rc;
+    if ((rc = dalloc(h, (void**)&h->d_delta[q], sizeof(float) * S * h->Mcap, "delta"))) return rc;
+    if ((rc = dalloc(h, (void**)&h->d_phi[q], sizeof(float) * S * h->nsub * h->Mcap, "phi"))) return rc;
+    if (h->rotation == CORR_ROT_PRE_F &&
+        (rc = dalloc(h, (void**)&h->d_dphi[q], sizeof(float2) * S * h->nsub * h->Mcap, "phase steps")))
+      return rc;
+    if ((rc = dalloc(h, (void**)&h->d_valid[q], (size_t)S * h->Mcap, "valid"))) return rc;
+    if ((rc = dalloc(h, (void**)&h->d_stat[q], sizeof(unsigned long long) * 3 * S, "stat"))) return rc;
+    CK(cudaMallocHost((void**)&h->h_stat[q], sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
+  }
+  CK(cudaMallocHost((void**)&h->h_stat_init, sizeof(unsigned long long) * 3 * S), "cudaMallocHost stat");
+  for (int s = 0; s < S; ++s) {
+    h->h_stat_init[3 * s + 0] = 0ull;   // max window end
+    h->h_stat_init[3 * s + 1] = ~0ull;  // min window start
+    h->h_stat_init[3 * s + 2] = 0ull;   // valid blocks
+  }
   if ((rc = dalloc(h, (void**)&h->d_twN, sizeof(float2) * h->N, "twiddles"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_spec, w.spec, "spectra"))) return rc;
+  h->overlap = w.nbuf == 2;
+  for (int q = 0; q < w.nbuf; ++q)
+    if ((rc = dalloc(h, (void**)&h->d_spec[q], w.spec, "spectra"))) return rc;
+  for (int q = 0; q < 2; ++q) {
+    CK(cudaEventCreateWithFlags(&h->ev_f[q], cudaEventDisableTiming), "events");
+    CK(cudaEventCreateWithFlags(&h->ev_x[q], cudaEventDisableTiming), "events");
+  }
+  CK(cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming), "events");
+  CK(cudaEventCreateWithFlags(&h->ev_la, cudaEventDisableTiming), "events");
   if ((rc = dalloc(h, (void**)&h->d_part, w.part, "partials"))) return rc;
-  if ((rc = dalloc(h, (void**)&h->d_out, sizeof(float2) * (size_t)nbl * G * nch, "out"))) return rc;
+  if ((rc = dalloc(h, (void**)&h->d_out, sizeof(float2) * (size_t)nbl * out_per_baseline(h), "out"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wcount, sizeof(int) * nbl, "wcount"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_wts, sizeof(double) * nbl, "weights"))) return rc;
   if ((rc = dalloc(h, (void**)&h->d_err, sizeof(int), "error flag"))) return rc;
@@ -371,9 +455,11 @@ static int prepare(corr_t* h) {
   h->tc_tiles = w.tiles;
   h->tc_direct = w.direct;
   if (h->tc_tiles) {
-    if ((rc = dalloc(h, (void**)&h->d_tiles, w.tiles_bytes, "operand tiles"))) return rc;
-    // rows beyond the stations of a tile stay zero for good
-    CK(cudaMemset(h->d_tiles, 0, w.tiles_bytes), "operand tiles clear");
+    for (int q = 0; q < w.nbuf; ++q) {
+      if ((rc = dalloc(h, (void**)&h->d_tiles[q], w.tiles_bytes, "operand tiles"))) return rc;
+      // rows beyond the stations of a tile stay zero for good
+      CK(cudaMemset(h->d_tiles[q], 0, w.tiles_bytes), "operand tiles clear");
+    }
   }
   *h->h_err = 0;
   CK(cudaMemset(h->d_err, 0, sizeof(int)), "error flag reset");
@@ -394,6 +480,10 @@ static int upload_model(corr_t* h) {
   for (int s = 0; s < S; ++s)
     if (h->st[s].segs.empty()) return h->fail(CORR_EINVAL, "station %d has no delay polynomial", s);
   if (h->polys_dirty) {
+    // a look-ahead delay evaluation may still read the old model
+    int rc0 = drop_lookahead(h);
+    if (rc0) return rc0;
+    h->model_gen += 1;
     std::vector<int> nseg(S);
     std::vector<double> t0((size_t)S * kMaxSegs, 0.0), c((size_t)S * kMaxSegs * 6, 0.0);
     for (int s = 0; s < S; ++s) {
@@ -423,6 +513,10 @@ static int upload_model(corr_t* h) {
     v.ngroups = station_groups(h, x);
   }
   if (h->views_valid && memcmp(views.data(), h->h_views, sizeof(StationView) * S) == 0) return CORR_OK;
+  // the F step and a look-ahead delay evaluation may still read the old views
+  int rc1 = drop_lookahead(h);
+  if (rc1) return rc1;
+  h->model_gen += 1;
   CK(cudaStreamSynchronize(h->stream), "sync before view update");
   memcpy(h->h_views, views.data(), sizeof(StationView) * S);
   CK(cudaMemcpyAsync(h->d_views, h->h_views, sizeof(StationView) * S, cudaMemcpyHostToDevice, h->stream),
@@ -431,7 +525,7 @@ static int upload_model(corr_t* h) {
   return CORR_OK;
 }
 
-static DelayParams delay_params(corr_t* h, int64_t b0, int nb, int ld) {
+static DelayParams delay_params(corr_t* h, int64_t b0, int nb, int ld, int slot) {
   DelayParams p;
   p.S = h->S;
   p.nsub = h->nsub;
@@ -445,23 +539,27 @@ static DelayParams delay_params(corr_t* h, int64_t b0, int nb, int ld) {
   p.b0 = b0;
   p.nb = nb;
   p.ld = ld;
-  p.start = h->d_start;
-  p.delta = h->d_delta;
-  p.phi = h->d_phi;
-  p.valid = h->d_valid;
+  p.start = h->d_start[slot];
+  p.delta = h->d_delta[slot];
+  p.phi = h->d_phi[slot];
+  p.valid = h->d_valid[slot];
   p.eps_out = nullptr;
   p.tau_out = nullptr;
   p.max_end = nullptr;
+  p.dphi = h->d_dphi[slot];  // null unless pre-F
   return p;
 }
 
-static FParams fparams(corr_t* h, int blk0, int cb) {
+static FParams fparams(corr_t* h, int blk0, int cb, int slot) {
   FParams p;
   p.st = h->d_views;
-  p.start = h->d_start;
-  p.delta = h->d_delta;
-  p.phi = h->d_phi;
-  p.valid = h->d_valid;
+  p.start = h->d_start[slot];
+  p.delta = h->d_delta[slot];
+  p.phi = h->d_phi[slot];
+  p.valid = h->d_valid[slot];
+  p.dphi = h->d_dphi[slot];
+  p.pre = h->rotation == CORR_ROT_PRE_F ? 1 : 0;
+  p.cross = cross_of(h) ? 1 : 0;
   p.ld = h->Mcap;
   p.blk0 = blk0;
   p.CB = cb;
@@ -477,91 +575,118 @@ static FParams fparams(corr_t* h, int blk0, int cb) {
   p.twN = h->d_twN;
   p.out_kind = 0;
   p.scale = 1.0f;
-  p.out = h->d_spec;
+  p.out = h->d_spec[0];
   return p;
 }
 
-// Device work of one integration after its delay blocks are in the
-// descriptor arrays: partial-sum clear, F and X per chunk, weights and
-// normalisation, all on stream st, with no host wait (so it can be recorded
-// into a CUDA graph).  M = blocks of the integration.
-static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, double* w_out) {
+// Device work of one integration after its delay blocks are in descriptor
+// slot `slot`: partial-sum clear, F and X per chunk, weights and
+// normalisation, with no host wait (so it can be recorded into a CUDA graph).
+// M = blocks of the integration.  With `overlap` the X step of each chunk
+// runs on xstream while the F step of the next chunk runs on st (two
+// spectra / tile buffers, events between them); everything joins st again
+// before the weights.  Without it every launch goes to st.
+static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, double* w_out, int slot, bool overlap) {
   const int S = h->S;
   cudaEvent_t pa = nullptr;
-  // F and X per chunk
-  const int nbl = nbl_of(S);
   const bool tc = h->precision != CORR_PREC_FP32;
   const bool fp8 = h->precision == CORR_PREC_FP8_TC;
   const int kz_used = tc ? 1 : h->KZ;
-  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl * h->G * h->nchan, st),
+  // the X step's stations and streams (2S and nsub with both hands)
+  const int XS = x_stations(h), XG = x_streams(h);
+  cudaStream_t xs = overlap ? h->xstream : st;
+  CK(cudaMemsetAsync(h->d_part, 0, sizeof(float2) * (size_t)kz_used * nbl_of(XS) * XG * h->nchan, st),
      "partials memset");
-  for (int c0 = 0; c0 < M; c0 += h->CB) {
+  int c = 0;
+  for (int c0 = 0; c0 < M; c0 += h->CB, ++c) {
+    const int buf = overlap ? (c & 1) : 0;
     const int cb = (M - c0 < h->CB) ? (M - c0) : h->CB;
-    FParams fp = fparams(h, c0, cb);
+    // the F step writes buffer `buf`: the X step that read it last must be done
+    if (overlap && h->x_pending[buf]) {
+      CK(cudaStreamWaitEvent(st, h->ev_x[buf], 0), "wait for the X step");
+      h->x_pending[buf] = false;
+    }
+    FParams fp = fparams(h, c0, cb, slot);
+    fp.out = h->d_spec[buf];
     if (tc) {
       fp.out_kind = fp8 ? 2 : 1;
       fp.scale = ldexpf(1.0f, -h->sigma);
     }
     if (h->tc_tiles) {
       // MMA operand tiles, fetched by the X step with bulk copies: written by
-      // the F step itself, or corner-turned from FP16 spectra
+      // the F step itself, or corner-turned from FP16 / FP8 spectra
       TcTiles o;
-      o.tiles = h->d_tiles;
-      o.cpt = xtc_cpt(S);
+      o.tiles = h->d_tiles[buf];
+      o.cpt = xtc_cpt(XS);
       o.W = 2 * o.cpt;
       o.nslice = (h->nchan + o.W - 1) / o.W;
       o.fp8 = fp8 ? 1 : 0;
       o.NKT = fp8 ? (cb + 127) / 128 : (cb + 63) / 64;
       o.scale = ldexpf(1.0f, -h->sigma);
-      pa = prof_begin(h);
+      pa = prof_begin(h, st);
       if (h->tc_direct) {
         CK(launch_fstage_tc(fp, o, st), "tensor-core fstage launch");
       } else {
         CK(launch_fstage(fp, st), "fstage launch");
         if (fp8)
-          CK(launch_tiles8(reinterpret_cast<const uint16_t*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
+          CK(launch_tiles8(reinterpret_cast<const uint16_t*>(h->d_spec[buf]), o, cb, cb, XS, XG, h->nchan, st),
              "FP8 tile corner-turn launch");
         else
-          CK(launch_tiles(reinterpret_cast<const __half2*>(h->d_spec), o, cb, cb, S, h->G, h->nchan, st),
+          CK(launch_tiles(reinterpret_cast<const __half2*>(h->d_spec[buf]), o, cb, cb, XS, XG, h->nchan, st),
              "tile corner-turn launch");
       }
-      prof_end(h, 1, pa);
+      prof_end(h, 1, pa, st);
+      if (overlap) {
+        CK(cudaEventRecord(h->ev_f[buf], st), "F event");
+        CK(cudaStreamWaitEvent(xs, h->ev_f[buf], 0), "wait for the F step");
+      }
       XTC2Params xp;
-      xp.tiles = h->d_tiles;
+      xp.tiles = h->d_tiles[buf];
       xp.nslice = o.nslice;
       xp.NKT = o.NKT;
-      xp.S = S;
-      xp.G = h->G;
+      xp.S = XS;
+      xp.G = XG;
       xp.nchan = h->nchan;
       xp.cpt = o.cpt;
       xp.W = o.W;
       xp.fp8 = o.fp8;
       xp.part = h->d_part;
       xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xtc2(xp, h->sm_count, st), "tensor-core xstage launch");
-      prof_end(h, 2, pa);
-      continue;
-    }
-    pa = prof_begin(h);
-    CK(launch_fstage(fp, st), "fstage launch");
-    prof_end(h, 1, pa);
-    {
+      pa = prof_begin(h, xs);
+      CK(launch_xtc2(xp, h->sm_count, xs), "tensor-core xstage launch");
+      prof_end(h, 2, pa, xs);
+    } else {
+      pa = prof_begin(h, st);
+      CK(launch_fstage(fp, st), "fstage launch");
+      prof_end(h, 1, pa, st);
+      if (overlap) {
+        CK(cudaEventRecord(h->ev_f[buf], st), "F event");
+        CK(cudaStreamWaitEvent(xs, h->ev_f[buf], 0), "wait for the F step");
+      }
       XParams xp;
-      xp.spec = h->d_spec;
+      xp.spec = h->d_spec[buf];
       xp.CB = cb;
-      xp.S = S;
-      xp.G = h->G;
+      xp.S = XS;
+      xp.G = XG;
       xp.nchan = h->nchan;
       xp.KZ = h->KZ;
       xp.part = h->d_part;
       xp.err = h->d_err;
-      pa = prof_begin(h);
-      CK(launch_xstage(xp, st), "xstage launch");
-      prof_end(h, 2, pa);
+      pa = prof_begin(h, xs);
+      CK(launch_xstage(xp, xs), "xstage launch");
+      prof_end(h, 2, pa, xs);
+    }
+    if (overlap) {
+      CK(cudaEventRecord(h->ev_x[buf], xs), "X event");
+      h->x_pending[buf] = true;
     }
   }
-  // weights + normalisation
+  // every X step of the integration before the weights and normalisation
+  for (int q = 0; q < 2; ++q)
+    if (h->x_pending[q]) {
+      CK(cudaStreamWaitEvent(st, h->ev_x[q], 0), "wait for the X step");
+      h->x_pending[q] = false;
+    }
   FinParams fin;
   fin.part = h->d_part;
   fin.KZ = kz_used;
@@ -569,20 +694,43 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
   fin.G = h->G;
   fin.nchan = h->nchan;
   fin.N = h->N;
-  fin.valid = h->d_valid;
+  fin.valid = h->d_valid[slot];
   fin.ld = h->Mcap;
   fin.M = M;
   fin.wcount = h->d_wcount;
   fin.out = vis_out;
   fin.weights = w_out;
   fin.err = nullptr;  // the handle reports a device timeout as CORR_ETIMEOUT
-  pa = prof_begin(h);
+  pa = prof_begin(h, st);
   CK(launch_weights(fin, st), "weights launch");
-  if (tc)
+  if (cross_of(h)) {
+    fin.G = h->nsub;
+    CK(launch_finalize_cross(fin, tc, tc ? ldexpf(1.0f, 2 * h->sigma) : 1.0f, st), "finalize launch");
+  } else if (tc) {
     CK(launch_finalize_tc(fin, ldexpf(1.0f, 2 * h->sigma), st), "finalize launch");
-  else
+  } else {
     CK(launch_finalize(fin, st), "finalize launch");
-  prof_end(h, 3, pa);
+  }
+  prof_end(h, 3, pa, st);
+  return CORR_OK;
+}
+
+// Delay blocks of integration i into descriptor slot i & 1 on stream st,
+// with the data-coverage statistics copied to the slot's pinned host copy.
+static int enqueue_delays(corr_t* h, int64_t i, cudaStream_t st) {
+  const int S = h->S;
+  const int slot = (int)(i & 1);
+  const int64_t bfirst = integ_first_block(h, i);
+  const int M = (int)(integ_first_block(h, i + 1) - bfirst);
+  CK(cudaMemcpyAsync(h->d_stat[slot], h->h_stat_init, sizeof(unsigned long long) * 3 * S, cudaMemcpyHostToDevice, st),
+     "stat H2D");
+  DelayParams dp = delay_params(h, bfirst, M, h->Mcap, slot);
+  dp.max_end = h->d_stat[slot];
+  cudaEvent_t pa = prof_begin(h, st);
+  CK(launch_delay_blocks(dp, st), "delay_blocks launch");
+  prof_end(h, 0, pa, st);
+  CK(cudaMemcpyAsync(h->h_stat[slot], h->d_stat[slot], sizeof(unsigned long long) * 3 * S, cudaMemcpyDeviceToHost, st),
+     "stat D2H");
   return CORR_OK;
 }
 
@@ -595,33 +743,30 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   if ((rc = upload_model(h))) return rc;
   const int S = h->S;
   const int64_t i = h->next_int;
+  const int slot = (int)(i & 1);
   const int64_t bfirst = integ_first_block(h, i);
   const int M = (int)(integ_first_block(h, i + 1) - bfirst);
 
-  // 1. delay blocks + data-coverage statistics
-  for (int s = 0; s < S; ++s) {
-    h->h_stat[3 * s + 0] = 0ull;
-    h->h_stat[3 * s + 1] = ~0ull;
-    h->h_stat[3 * s + 2] = 0ull;
+  // 1. delay blocks + data-coverage statistics: evaluated ahead during the
+  //    previous integration (for the same model and data), or now
+  if (h->la_valid && h->la_int == i && h->la_gen == h->model_gen) {
+    CK(cudaEventSynchronize(h->ev_la), "look-ahead delay blocks");
+    CK(cudaStreamWaitEvent(h->stream, h->ev_la, 0), "wait for the delay blocks");
+    h->la_valid = false;
+  } else {
+    if ((rc = drop_lookahead(h))) return rc;
+    if ((rc = enqueue_delays(h, i, h->stream))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "delay_blocks");
   }
-  CK(cudaMemcpyAsync(h->d_stat, h->h_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyHostToDevice, h->stream),
-     "stat H2D");
-  DelayParams dp = delay_params(h, bfirst, M, h->Mcap);
-  dp.max_end = h->d_stat;
-  cudaEvent_t pa = prof_begin(h);
-  CK(launch_delay_blocks(dp, h->stream), "delay_blocks launch");
-  prof_end(h, 0, pa);
-  CK(cudaMemcpyAsync(h->h_stat, h->d_stat, sizeof(unsigned long long) * 3 * S, cudaMemcpyDeviceToHost, h->stream),
-     "stat D2H");
-  CK(cudaStreamSynchronize(h->stream), "delay_blocks");
   if (*h->h_err) return h->fail(CORR_ETIMEOUT, "an X-step wait timed out on the device");
   const unsigned long long off = 1ull << 62;
+  const unsigned long long* stat = h->h_stat[slot];
   // the compute stream waits for the asynchronous pushes holding the bytes
   // this integration reads (pieces that start below the last byte needed)
   for (int s = 0; s < S; ++s) {
     Station& x = h->st[s];
     if (x.pending.empty()) continue;
-    const int64_t need = (int64_t)(h->h_stat[3 * s + 0] - off);
+    const int64_t need = (int64_t)(stat[3 * s + 0] - off);
     const size_t need_bytes = need > 0 ? (size_t)((need * (int64_t)h->G * 2 + 7) / 8) : 0;
     size_t keep = 0;
     for (size_t q = 0; q < x.pending.size(); ++q) {
@@ -636,8 +781,8 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   }
   bool any_data = false;
   for (int s = 0; s < S; ++s) {
-    const int64_t need = (int64_t)(h->h_stat[3 * s + 0] - off);
-    const int64_t first = (int64_t)(h->h_stat[3 * s + 1] - off);
+    const int64_t need = (int64_t)(stat[3 * s + 0] - off);
+    const int64_t first = (int64_t)(stat[3 * s + 1] - off);
     const int64_t have = station_groups(h, h->st[s]);
     if (need > have && !h->flushed)
       return h->fail(CORR_EAGAIN, "station %d: integration %lld needs %lld sample groups, %lld present", s,
@@ -646,10 +791,21 @@ static int run_integration(corr_t* h, float2* vis_out, double* w_out) {
   }
   if (h->flushed && !any_data) return h->fail(CORR_EEND, "no station has data for integration %lld", (long long)i);
 
-  int rc2 = enqueue_rest(h, h->stream, M, vis_out, w_out);
+  // the other descriptor slot is free once everything enqueued so far
+  // (integration i-1's F and weights) has run
+  CK(cudaEventRecord(h->ev_main, h->stream), "main event");
+  int rc2 = enqueue_rest(h, h->stream, M, vis_out, w_out, slot, h->overlap);
   if (rc2) return rc2;
   CK(cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "error flag D2H");
   h->next_int = i + 1;
+  // 2. look-ahead: the next integration's delay blocks, on their own stream,
+  //    while this integration's F and X steps run
+  CK(cudaStreamWaitEvent(h->dstream, h->ev_main, 0), "look-ahead wait");
+  if ((rc = enqueue_delays(h, i + 1, h->dstream))) return rc;
+  CK(cudaEventRecord(h->ev_la, h->dstream), "look-ahead event");
+  h->la_valid = true;
+  h->la_int = i + 1;
+  h->la_gen = h->model_gen;
   return CORR_OK;
 }
 
@@ -699,9 +855,20 @@ int corr_create(corr_t** hp, int stations, int subbands, int pols, int nchan, do
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
   for (int q = 0; q < kCopyStreams && e == cudaSuccess; ++q)
     e = cudaStreamCreateWithFlags(&h->copy_stream[q], cudaStreamNonBlocking);
+  // the X step's stream gets the highest priority: its CTAs are placed first
+  // as the F step's retire, so the two overlap instead of running in turn
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->xstream, cudaStreamNonBlocking, prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->dstream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     g_create_error = std::string("corr_create: ") + cudaGetErrorString(e);
     cudaGetLastError();
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    for (int q = 0; q < kCopyStreams; ++q)
+      if (h->copy_stream[q]) cudaStreamDestroy(h->copy_stream[q]);
+    if (h->xstream) cudaStreamDestroy(h->xstream);
+    if (h->dstream) cudaStreamDestroy(h->dstream);
     delete h;
     return CORR_ECUDA;
   }
@@ -740,11 +907,47 @@ int corr_set_precision(corr_t* h, int mode) {
   if (!h) return CORR_EINVAL;
   if (mode != CORR_PREC_FP32 && mode != CORR_PREC_FP16_TC && mode != CORR_PREC_FP8_TC)
     return h->fail(CORR_EINVAL, "corr_set_precision: unknown mode %d", mode);
-  if (mode != CORR_PREC_FP32 && h->S > 64)
-    return h->fail(CORR_EINVAL, "corr_set_precision: the tensor-core X step takes at most 64 stations");
+  if (mode != CORR_PREC_FP32 && x_stations(h) > 64)
+    return h->fail(CORR_EINVAL, cross_of(h) ? "corr_set_precision: with both hands the tensor-core X step takes at most 32 stations"
+                                            : "corr_set_precision: the tensor-core X step takes at most 64 stations");
   if (h->prepared && mode != h->precision)
     return h->fail(CORR_ESTATE, "corr_set_precision: only before the first correlate");
   h->precision = mode;
+  return CORR_OK;
+}
+
+int corr_set_pol_products(corr_t* h, int mode) {
+  if (!h) return CORR_EINVAL;
+  if (mode != CORR_POL_PARALLEL && mode != CORR_POL_CROSS)
+    return h->fail(CORR_EINVAL, "corr_set_pol_products: unknown mode %d", mode);
+  if (mode == CORR_POL_CROSS && h->npol != 2)
+    return h->fail(CORR_EINVAL, "corr_set_pol_products: both hands need two polarisations");
+  if (mode == CORR_POL_CROSS && h->precision != CORR_PREC_FP32 && 2 * h->S > 64)
+    return h->fail(CORR_EINVAL, "corr_set_pol_products: with both hands the tensor-core X step takes at most 32 stations");
+  if (h->prepared && mode != h->pol_products)
+    return h->fail(CORR_ESTATE, "corr_set_pol_products: only before the first correlate");
+  h->pol_products = mode;
+  return CORR_OK;
+}
+
+int corr_set_fringe_rotation(corr_t* h, int mode) {
+  if (!h) return CORR_EINVAL;
+  if (mode != CORR_ROT_POST_F && mode != CORR_ROT_PRE_F)
+    return h->fail(CORR_EINVAL, "corr_set_fringe_rotation: unknown mode %d", mode);
+  if (mode == CORR_ROT_PRE_F && !fstage_pre_supported(h->nchan))
+    return h->fail(CORR_EINVAL, "corr_set_fringe_rotation: pre-F rotation takes at most 4096 channels");
+  if (h->prepared && mode != h->rotation)
+    return h->fail(CORR_ESTATE, "corr_set_fringe_rotation: only before the first correlate");
+  h->rotation = mode;
+  return CORR_OK;
+}
+
+int corr_set_pipeline(corr_t* h, int overlap) {
+  if (!h) return CORR_EINVAL;
+  if (overlap != 0 && overlap != 1) return h->fail(CORR_EINVAL, "corr_set_pipeline: overlap must be 0 or 1");
+  if (h->prepared && overlap != h->pipeline)
+    return h->fail(CORR_ESTATE, "corr_set_pipeline: only before the first correlate");
+  h->pipeline = overlap;
   return CORR_OK;
 }
 
@@ -949,7 +1152,7 @@ int corr_correlate(corr_t* h, float* out, double* weights) {
   double* dw = weights ? h->d_wts : nullptr;
   rc = run_integration(h, h->d_out, dw);
   if (rc == CORR_OK) {
-    const size_t bytes = sizeof(float2) * (size_t)nbl_of(h->S) * h->G * h->nchan;
+    const size_t bytes = sizeof(float2) * (size_t)nbl_of(h->S) * out_per_baseline(h);
     cudaError_t e = cudaMemcpyAsync(out, h->d_out, bytes, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && dw)
       e = cudaMemcpyAsync(weights, dw, sizeof(double) * nbl_of(h->S), cudaMemcpyDeviceToHost, h->stream);
@@ -975,7 +1178,7 @@ int corr_next_integration(const corr_t* h, int64_t* index) {
 int corr_rewind(corr_t* h) {
   if (!h) return CORR_EINVAL;
   h->next_int = 0;
-  return CORR_OK;
+  return CORR_OK;  // a look-ahead for another integration is dropped by the next correlate
 }
 
 int corr_reset(corr_t* h) {
@@ -983,6 +1186,8 @@ int corr_reset(corr_t* h) {
   int rc = use_device(h);
   if (rc) return rc;
   cudaStreamSynchronize(h->stream);
+  if (h->xstream) cudaStreamSynchronize(h->xstream);
+  drop_lookahead(h);
   drain_pushes(h);
   for (Station& s : h->st) {
     for (auto& pe : s.pending) cudaEventDestroy(pe.ev);
@@ -1020,6 +1225,8 @@ void corr_destroy(corr_t* h) {
   cudaGetDevice(&cur);
   if (cur != h->dev) cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->xstream) cudaStreamSynchronize(h->xstream);
+  if (h->dstream) cudaStreamSynchronize(h->dstream);
   drain_pushes(h);
   for (Station& s : h->st) {
     for (auto& pe : s.pending) cudaEventDestroy(pe.ev);
@@ -1032,6 +1239,8 @@ void corr_destroy(corr_t* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   free_device(h);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  if (h->xstream) cudaStreamDestroy(h->xstream);
+  if (h->dstream) cudaStreamDestroy(h->dstream);
   for (int q = 0; q < kCopyStreams; ++q)
     if (h->copy_stream[q]) cudaStreamDestroy(h->copy_stream[q]);
   if (cur != h->dev && cur >= 0) cudaSetDevice(cur);
@@ -1084,12 +1293,13 @@ int corr_batch_run(corr_t* const* hs, int n, float* const* dev_out, double* cons
   for (int j = 0; j < n; ++j) {
     corr_t* h = hs[j];
     int rc;
-    if ((rc = prepare(h)) || (rc = upload_model(h)) || (rc = drain_pushes(h))) return rc;
+    if ((rc = prepare(h)) || (rc = upload_model(h)) || (rc = drain_pushes(h)) || (rc = drop_lookahead(h))) return rc;
     for (Station& x : h->st) {
       for (auto& pe : x.pending) cudaEventDestroy(pe.ev);
       x.pending.clear();
     }
     CK(cudaStreamSynchronize(h->stream), "corr_batch_run: handle stream");
+    CK(cudaStreamSynchronize(h->xstream), "corr_batch_run: handle stream");
     if (*h->h_err) return h->fail(CORR_ETIMEOUT, "an X-step wait timed out on the device");
   }
   cudaStream_t root = cuda_stream ? (cudaStream_t)cuda_stream : b.st[0];
@@ -1108,9 +1318,12 @@ int corr_batch_run(corr_t* const* hs, int n, float* const* dev_out, double* cons
     const int64_t bfirst = integ_first_block(h, i);
     const int M = (int)(integ_first_block(h, i + 1) - bfirst);
     bad = j;
-    e = launch_delay_blocks(delay_params(h, bfirst, M, h->Mcap), st);
+    const int slot = (int)(i & 1);
+    e = launch_delay_blocks(delay_params(h, bfirst, M, h->Mcap, slot), st);
     if (e != cudaSuccess) break;
-    rc = enqueue_rest(h, st, M, reinterpret_cast<float2*>(dev_out[j]), dev_weights ? dev_weights[j] : nullptr);
+    // one stream per scan inside the graph (scans run side by side instead)
+    rc = enqueue_rest(h, st, M, reinterpret_cast<float2*>(dev_out[j]), dev_weights ? dev_weights[j] : nullptr, slot,
+                      false);
     if (rc == CORR_OK) e = cudaMemcpyAsync(h->h_err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
   }
   // join every branch back into the root
@@ -1205,6 +1418,7 @@ int corr_debug_delays(corr_t* h, int64_t b0, int64_t nb, int64_t* start, double*
   int64_t* d_start = nullptr;
   float* d_delta = nullptr;
   float* d_phi = nullptr;
+  float2* d_dphi = nullptr;  // pre-F: phase step per sample (hi, lo), [S][nsub][Mcap]
   uint8_t* d_valid = nullptr;
   double *d_eps = nullptr, *d_tau = nullptr;
   const size_t n = (size_t)S * nb;
@@ -1214,13 +1428,14 @@ int corr_debug_delays(corr_t* h, int64_t b0, int64_t nb, int64_t* start, double*
     cudaFree(d_start); cudaFree(d_delta); cudaFree(d_phi); cudaFree(d_valid); cudaFree(d_eps); cudaFree(d_tau);
     return rc;
   }
-  DelayParams p = delay_params(h, b0, (int)nb, (int)nb);
+  DelayParams p = delay_params(h, b0, (int)nb, (int)nb, 0);
   p.start = d_start;
   p.delta = d_delta;
   p.phi = d_phi;
   p.valid = d_valid;
   p.eps_out = d_eps;
   p.tau_out = d_tau;
+  p.dphi = nullptr;  // phi: the phase at the block centre
   cudaError_t e = launch_delay_blocks(p, h->stream);
   if (e == cudaSuccess && start) e = cudaMemcpyAsync(start, d_start, n * 8, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess && eps) e = cudaMemcpyAsync(eps, d_eps, n * 8, cudaMemcpyDeviceToHost, h->stream);
@@ -1253,23 +1468,25 @@ int corr_debug_spectrum(corr_t* h, int station, int stream, int64_t block, float
   if (station < 0 || station >= h->S || stream < 0 || stream >= h->G || !out)
     return h->fail(CORR_EINVAL, "corr_debug_spectrum: bad argument");
   int rc;
-  if ((rc = use_device(h)) || (rc = prepare(h)) || (rc = upload_model(h))) return rc;
+  if ((rc = use_device(h)) || (rc = prepare(h)) || (rc = upload_model(h)) || (rc = drop_lookahead(h))) return rc;
   // one-block pass through the same kernels, in the handle's work buffers
-  DelayParams dp = delay_params(h, block, 1, h->Mcap);
+  // (descriptor slot 0, which the next correlate call fills again)
+  DelayParams dp = delay_params(h, block, 1, h->Mcap, 0);
   CK(launch_delay_blocks(dp, h->stream), "delay_blocks");
   // a buffer of its own: in tensor-core tile mode the handle has no FP32
   // spectra buffer
   float2* spec = nullptr;
   if ((rc = dalloc(h, (void**)&spec, sizeof(float2) * (size_t)h->G * h->S * h->nchan, "debug spectrum"))) return rc;
-  FParams fp = fparams(h, 0, 1);
+  FParams fp = fparams(h, 0, 1, 0);
   fp.out = spec;
+  fp.cross = 0;  // [stream][block][station]
   cudaError_t e = launch_fstage(fp, h->stream);
   const float2* src = spec + ((size_t)stream * 1 * h->S + station) * h->nchan;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(out, src, sizeof(float2) * h->nchan, cudaMemcpyDeviceToHost, h->stream);
   uint8_t v = 0;
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&v, h->d_valid + (size_t)station * h->Mcap, 1, cudaMemcpyDeviceToHost, h->stream);
+    e = cudaMemcpyAsync(&v, h->d_valid[0] + (size_t)station * h->Mcap, 1, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(spec);
   if (e != cudaSuccess) return h->cuda_fail(e, "corr_debug_spectrum");

@@ -44,6 +44,10 @@ struct DelayParams {
   uint8_t* valid;
   double* eps_out;          // optional (debug): eps in seconds
   double* tau_out;          // optional (debug): tau in seconds
+  // optional, pre-F rotation ([S][nsub][ld]): when set, phi holds the phase at
+  // the block's first sample instead of its centre, and dphi the phase step
+  // per sample in turns as (hi, lo) with hi of at most 10 significant bits
+  float2* dphi;
   unsigned long long* max_end;   // optional [S]: max(window end - sample0) over blocks, encoded +2^62
 };
 
@@ -54,6 +58,9 @@ struct FParams {
   const float* delta;       // [S][ld]
   const float* phi;         // [S][nsub][ld]
   const uint8_t* valid;     // [S][ld]
+  const float2* dphi;       // [S][nsub][ld] (pre-F only): phase step per sample, (hi, lo) turns
+  int pre;                  // 1: pre-F fringe rotation (phi = phase at the block's first sample)
+  int cross;                // 1: spectra in [subband][block][pol][station] order (both hands)
   int ld;
   int blk0;                 // first block of the chunk (index into descriptor arrays)
   int CB;                   // blocks in chunk
@@ -120,6 +127,10 @@ cudaError_t fstage_ensure_constants();
 unsigned long long current_context_id();
 bool fstage_supported(int nchan);
 cudaError_t launch_fstage(const FParams& p, cudaStream_t s);
+// the pre-F variant (p.pre != 0), nchan <= 4096; launch_fstage dispatches to it
+bool fstage_pre_supported(int nchan);
+cudaError_t launch_fstage_pre(const FParams& p, cudaStream_t s);
+cudaError_t fstage_pre_init_constants();
 int xstage_kz(int CB, int S, int G, int nchan);
 cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
 cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
@@ -140,6 +151,10 @@ cudaError_t launch_tiles8(const uint16_t* spec8, const TcTiles& o, int CB, int c
                           cudaStream_t s);
 // finalise for the tensor-core layout [KZ][G][nchan][nbl]; `unscale` undoes the FP16 pre-scale
 cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s);
+// finalise of both hands: partials over 2 p.S virtual stations v = pol * S + station and
+// p.G = nsub streams (FP32 layout [KZ][nblv][nsub][nchan], or with `tc` the tensor-core
+// layout [KZ][nsub][nchan][nblv]); out [nbl][nsub][4][nchan], hand product pq = 2 p + q
+cudaError_t launch_finalize_cross(const FinParams& p, bool tc, float unscale, cudaStream_t s);
 
 __host__ __device__ inline int nbl_of(int S) { return S * (S + 1) / 2; }
 __host__ __device__ inline int bl_index(int a, int b, int S) { return a * S - a * (a - 1) / 2 + (b - a); }

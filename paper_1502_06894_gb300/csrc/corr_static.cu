@@ -212,6 +212,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
   dp.eps_out = nullptr;
   dp.tau_out = nullptr;
   dp.max_end = nullptr;
+  dp.dphi = nullptr;
   e = launch_delay_blocks(dp, st);
   for (int c0 = 0; e == cudaSuccess && c0 < M; c0 += CB) {
     const int cb = (M - c0 < CB) ? (M - c0) : CB;
@@ -221,6 +222,9 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
     fp.delta = dp.delta;
     fp.phi = dp.phi;
     fp.valid = dp.valid;
+    fp.dphi = nullptr;
+    fp.pre = 0;
+    fp.cross = 0;
     fp.ld = M;
     fp.blk0 = c0;
     fp.CB = cb;

@@ -50,10 +50,35 @@ __global__ void k_delay_blocks(DelayParams p) {
   p.start[o] = start;
   p.valid[o] = ok ? 1 : 0;
   p.delta[o] = (float)__ddiv_rn(__dmul_rn(eps, p.fs), (double)N);
+  // pre-F rotation: the delay rate at t_c (derivative of the same segment)
+  double rate = 0.0;
+  if (p.dphi) {
+#pragma unroll
+    for (int q = 5; q >= 1; --q) rate = __fma_rn(rate, u, (double)q * c[q]);
+  }
   for (int sb = 0; sb < p.nsub; ++sb) {
     double ph = __dmul_rn(p.nu0[sb], tau);
     ph = __dsub_rn(ph, floor(ph));
-    p.phi[((size_t)s * p.nsub + sb) * p.ld + i] = (float)ph;
+    const size_t os = ((size_t)s * p.nsub + sb) * p.ld + i;
+    if (p.dphi) {
+      // phase step per sample (turns) and the phase at the block's first
+      // sample, N/2 samples before the centre; the step splits into a part of
+      // at most 10 significant bits (exact times any sample index < 2^14 in
+      // FP32) and the rest
+      const double step = p.nu0[sb] * rate / p.fs;
+      double p0 = ph - step * (double)(N / 2);
+      p0 -= floor(p0);
+      double hi = 0.0;
+      if (step != 0.0) {
+        int ex = 0;
+        frexp(step, &ex);
+        hi = ldexp(rint(ldexp(step, 10 - ex)), ex - 10);
+      }
+      p.phi[os] = (float)p0;
+      p.dphi[os] = make_float2((float)hi, (float)(step - hi));
+    } else {
+      p.phi[os] = (float)ph;
+    }
   }
   if (p.eps_out) p.eps_out[o] = eps;
   if (p.tau_out) p.tau_out[o] = tau;

@@ -97,4 +97,58 @@ cudaError_t launch_finalize_tc(const FinParams& p, float unscale, cudaStream_t s
   return cudaGetLastError();
 }
 
+// Both hands of two polarisations.  The X step ran over 2S virtual stations
+// v = pol * S + station per subband, so V_ab^pq is the virtual product
+// P[p S + a][q S + b] when p S + a <= q S + b and its conjugate otherwise
+// (for a = b and pq = 10: the conjugate of the 01 product).
+template <bool TC>
+__global__ void k_finalize_cross(FinParams p, float unscale) {
+  const int S = p.S, S2 = 2 * S, nsub = p.G, nch = p.nchan;
+  const int nblv = nbl_of(S2);
+  const size_t total = (size_t)nbl_of(S) * nsub * 4 * nch;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const int k = (int)(e % nch);
+    size_t r = e / nch;
+    const int pq = (int)(r & 3);
+    r >>= 2;
+    const int sb = (int)(r % nsub);
+    const int bl = (int)(r / nsub);
+    int a = 0, q = bl;
+    while (q >= S - a) { q -= S - a; ++a; }
+    const int b = a + q;
+    int v1 = (pq >> 1) * S + a, v2 = (pq & 1) * S + b;
+    const bool flip = v1 > v2;
+    if (flip) {
+      const int t = v1;
+      v1 = v2;
+      v2 = t;
+    }
+    const int blv = bl_index(v1, v2, S2);
+    float2 v = make_float2(0.f, 0.f);
+    for (int kz = 0; kz < p.KZ; ++kz) {
+      const float2 x = TC ? p.part[(((size_t)kz * nsub + sb) * nch + k) * nblv + blv]
+                          : p.part[(((size_t)kz * nblv + blv) * nsub + sb) * nch + k];
+      v.x += x.x;
+      v.y += x.y;
+    }
+    if (flip) v.y = -v.y;
+    const int w = p.wcount[bl];
+    const float sc = w > 0 ? (float)((double)unscale / ((double)w * (double)p.N)) : 0.f;
+    p.out[e] = make_float2(v.x * sc, v.y * sc);
+  }
+}
+
+cudaError_t launch_finalize_cross(const FinParams& p, bool tc, float unscale, cudaStream_t s) {
+  const size_t total = (size_t)nbl_of(p.S) * p.G * 4 * p.nchan;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  if (tc)
+    k_finalize_cross<true><<<blocks, 256, 0, s>>>(p, unscale);
+  else
+    k_finalize_cross<false><<<blocks, 256, 0, s>>>(p, unscale);
+  return cudaGetLastError();
+}
+
 }  // namespace corr
