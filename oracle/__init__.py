@@ -39,7 +39,7 @@ class _Scan(C.Structure):
         ("nu0", C.c_void_p), ("nseg", C.c_void_p), ("seg_t0", C.c_void_p), ("seg_c", C.c_void_p),
         ("maxseg", C.c_int),
         ("bytes", C.c_void_p), ("byte_off", C.c_void_p), ("sample0", C.c_void_p), ("nsamp", C.c_void_p),
-        ("rotation", C.c_int),
+        ("rotation", C.c_int), ("frame_payload", C.c_int),
     ]
 
 ROT_POST_F = 0   # fringe rotation after the transform, at the block centre (the default)
@@ -81,7 +81,8 @@ class Oracle:
 
     def __init__(self, stations: int, nsub: int, npol: int, nchan: int, fs: float, tint: float,
                  nu0: Sequence[float], polys, streams: Sequence[np.ndarray],
-                 sample0: Sequence[int], nsamp: Sequence[int], lut=DEFAULT_LUT, rotation: int = ROT_POST_F):
+                 sample0: Sequence[int], nsamp: Sequence[int], lut=DEFAULT_LUT, rotation: int = ROT_POST_F,
+                 frame_payload: int = 0):
         S = stations
         self.S, self.nsub, self.npol, self.nchan = S, nsub, npol, nchan
         self.G = nsub * npol
@@ -108,7 +109,9 @@ class Oracle:
         self._lens = [len(b) for b in streams]
         self._sc = _Scan(S, nsub, npol, nchan, self.fs, self.tint, (C.c_double * 4)(*lut),
                          _ptr(self._nu0), _ptr(self._nseg), _ptr(self._t0), _ptr(self._c), maxseg,
-                         _ptr(self._bytes), _ptr(self._off), _ptr(self._s0), _ptr(self._ns), int(rotation))
+                         _ptr(self._bytes), _ptr(self._off), _ptr(self._s0), _ptr(self._ns), int(rotation),
+                         int(frame_payload))
+        self.frame_payload = int(frame_payload)
 
     @classmethod
     def from_scan(cls, scan, streams, lut=DEFAULT_LUT, nsamp=None, rotation=ROT_POST_F):
@@ -133,6 +136,8 @@ class Oracle:
 
     def _check_bytes(self):
         for s, n in enumerate(self._lens):
+            if self.frame_payload > 0:   # payload bytes of the whole frames present
+                n = (n // (16 + self.frame_payload)) * self.frame_payload
             if self._ns[s] * self.G * 2 > n * 8:
                 raise ValueError("station %d: %d groups need more than %d bytes" % (s, self._ns[s], n))
 

@@ -17,14 +17,19 @@
  *   packing   code of stream j at sample-time t sits at bit 2*(t*G + j) of a
  *             little-endian bit stream (LSB first); G = nsub*npol streams,
  *             j = sb*npol + pol; a 4-entry table maps codes to levels.
+ *   frames    (selectable) Mark5B-style framing: the station's bytes are frames
+ *             of a 16-byte header and P payload bytes; the payloads in frame
+ *             order form the bit stream above; a frame is valid when its first
+ *             header word (32-bit little-endian) is the sync word 0xABADDEED.
  *   time      seconds relative to the scan epoch; block b spans geocentric
  *             samples [b*N, b*N + N), centre t_c = (b*N + N/2)/fs.
  *   delay     segment = largest t0 <= t_c; tau by Horner from c5 with fma at
  *             every step; n_b = floor(fma(tau, fs, 0.5)); eps = tau - n_b/fs;
  *             the block reads station samples [b*N + n_b, b*N + n_b + N).
  *   validity  a block is valid at a station when its window lies inside the
- *             station's samples and t_c >= the first segment's t0; a
- *             baseline's weight counts blocks valid at both ends.
+ *             station's samples and t_c >= the first segment's t0 (and, for
+ *             framed input, every frame holding one of its samples is valid);
+ *             a baseline's weight counts blocks valid at both ends.
  *   integr.   block b belongs to integration floor(b*N / SPI), with
  *             SPI = fs*tint samples per integration (an integer).
  *   spectrum  X[k] = sum_n x[n] exp(-2 pi i k n / N), k = 0..N/2-1 (DC kept,
@@ -74,7 +79,11 @@ typedef struct {
   const int64_t *sample0; /* [S] station sample index of the first group    */
   const int64_t *nsamp;   /* [S] number of sample-time groups present       */
   int rotation;           /* 0: post-F fringe rotation, 1: pre-F            */
+  int frame_payload;      /* 0: plain packed bytes; P > 0: frames of 16 + P bytes */
 } oracle_scan;
+
+#define ORACLE_SYNC 0xABADDEEDu
+#define ORACLE_HEADER 16
 
 /* ------------------------------------------------------------------------ */
 /* Unpacking (the packing reading above).                                   */
@@ -82,6 +91,27 @@ typedef struct {
 int oracle_code(const uint8_t *bytes, int G, int64_t t, int j) {
   int64_t bit = 2 * (t * (int64_t)G + j);
   return (bytes[bit >> 3] >> (bit & 7)) & 3;
+}
+
+/* The same code from a framed stream: payload byte q of the bit stream sits in
+ * frame q / P at offset 16 + q % P. */
+static int framed_code(const uint8_t *raw, int P, int G, int64_t t, int j) {
+  int64_t bit = 2 * (t * (int64_t)G + j);
+  int64_t q = bit >> 3;
+  int64_t f = q / P;
+  return (raw[f * (ORACLE_HEADER + P) + ORACLE_HEADER + (q - f * P)] >> (bit & 7)) & 3;
+}
+
+static int frame_valid(const uint8_t *raw, int P, int64_t f) {
+  const uint8_t *h = raw + f * (int64_t)(ORACLE_HEADER + P);
+  uint32_t w = (uint32_t)h[0] | ((uint32_t)h[1] << 8) | ((uint32_t)h[2] << 16) | ((uint32_t)h[3] << 24);
+  return w == ORACLE_SYNC;
+}
+
+static int sample_code(const oracle_scan *sc, int s, int64_t t, int j) {
+  const uint8_t *bytes = sc->bytes + sc->byte_off[s];
+  const int G = sc->nsub * sc->npol;
+  return sc->frame_payload > 0 ? framed_code(bytes, sc->frame_payload, G, t, j) : oracle_code(bytes, G, t, j);
 }
 
 /* codes of stream j for sample-time groups [t0, t0+count) of one station. */
@@ -129,7 +159,18 @@ static oracle_delay block_delay(const oracle_scan *sc, int s, int64_t b) {
 static int block_valid(const oracle_scan *sc, int s, int64_t b, const oracle_delay *d) {
   const int N = 2 * sc->nchan;
   int64_t i0 = b * (int64_t)N + d->nstart;
-  return d->covered && i0 >= sc->sample0[s] && i0 + N <= sc->sample0[s] + sc->nsamp[s];
+  if (!(d->covered && i0 >= sc->sample0[s] && i0 + N <= sc->sample0[s] + sc->nsamp[s])) return 0;
+  if (sc->frame_payload > 0) {
+    /* every frame holding a sample of the window must be valid */
+    const int G = sc->nsub * sc->npol, P = sc->frame_payload;
+    const uint8_t *raw = sc->bytes + sc->byte_off[s];
+    for (int64_t t = i0 - sc->sample0[s]; t < i0 - sc->sample0[s] + N; ++t)
+      for (int j = 0; j < G; ++j) {
+        int64_t q = (2 * (t * (int64_t)G + j)) >> 3;
+        if (!frame_valid(raw, P, q / P)) return 0;
+      }
+  }
+  return 1;
 }
 
 /* Per (station, block): n_b, eps, tau, validity and (if rate != NULL) the
@@ -205,7 +246,6 @@ static int station_spectrum(const oracle_scan *sc, int s, int j, int64_t b,
     memset(xi, 0, sizeof(double) * sc->nchan);
     return 0;
   }
-  const uint8_t *bytes = sc->bytes + sc->byte_off[s];
   int64_t t0 = b * (int64_t)N + d.nstart - sc->sample0[s];
   double nu0 = sc->nu0[j / sc->npol];
   double phi = fringe_turns(nu0, d.tau);
@@ -214,7 +254,7 @@ static int station_spectrum(const oracle_scan *sc, int s, int j, int64_t b,
     double per_sample = nu0 * d.rate / sc->fs;
     for (int n = 0; n < N; ++n) {
       double a = 2.0 * ORACLE_PI * (phi + per_sample * (double)(n - N / 2));
-      double x = sc->lut[oracle_code(bytes, G, t0 + n, j)];
+      double x = sc->lut[sample_code(sc, s, t0 + n, j)];
       re[n] = x * cos(a);
       im[n] = x * sin(a);
     }
@@ -229,7 +269,7 @@ static int station_spectrum(const oracle_scan *sc, int s, int j, int64_t b,
     return 1;
   }
   for (int n = 0; n < N; ++n) {
-    re[n] = sc->lut[oracle_code(bytes, G, t0 + n, j)];
+    re[n] = sc->lut[sample_code(sc, s, t0 + n, j)];
     im[n] = 0.0;
   }
   oracle_fft(re, im, N, 0);

@@ -301,6 +301,33 @@ def station_codes(scan: Scan, s: int, physics: bool = True) -> np.ndarray:
     return out
 
 
+MARK5B_SYNC = 0xABADDEED
+MARK5B_HEADER = 16
+MARK5B_PAYLOAD = 10000
+
+
+def frame(payload: np.ndarray, P: int = MARK5B_PAYLOAD, invalid=(), seconds0: int = 0) -> np.ndarray:
+    """Mark5B-style frames of a packed byte stream: frames of a 16-byte header
+    and P payload bytes (the last payload zero-padded).  Header word 0 is the
+    sync word (little-endian) except in the frames listed in `invalid`, which
+    carry 0 there (a lost or filled frame); word 1 holds the frame number in
+    its low 15 bits, word 2 a seconds count; word 3 stays 0."""
+    payload = np.asarray(payload, np.uint8)
+    nf = -(-payload.size // P)
+    out = np.zeros((nf, MARK5B_HEADER + P), np.uint8)
+    body = np.zeros(nf * P, np.uint8)
+    body[:payload.size] = payload
+    out[:, MARK5B_HEADER:] = body.reshape(nf, P)
+    words = np.zeros((nf, 4), np.uint32)
+    words[:, 0] = MARK5B_SYNC
+    words[:, 1] = np.arange(nf, dtype=np.uint32) & 0x7FFF
+    words[:, 2] = seconds0
+    for f in invalid:
+        words[f, 0] = 0
+    out[:, :MARK5B_HEADER] = words.view(np.uint8).reshape(nf, MARK5B_HEADER)
+    return out.reshape(-1)
+
+
 def station_bytes(scan: Scan, s: int, physics: bool = True) -> np.ndarray:
     return pack(station_codes(scan, s, physics))
 
