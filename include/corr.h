@@ -77,10 +77,15 @@ enum {
  * trade a stated error against the FP64 definition for tensor-core speed. */
 enum { CORR_PREC_FP32 = 0, CORR_PREC_FP16_TC = 1, CORR_PREC_FP8_TC = 2 };
 
-/* Create a correlator for one scan.  stations 1..256, subbands*pols 1..32,
- * pols 1 or 2, nchan a power of two in 4..8192, tint_s > 0.  *h receives the
- * handle (NULL on failure).  Allocates host state only; device memory is
- * allocated at the first corr_correlate* call. */
+/* Create a correlator for one scan: the FX correlation the paper's Abstract
+ * describes (each station's samples Fourier transformed, then every station
+ * pair cross-multiplied and accumulated), for `stations` stations recording
+ * `subbands` subbands in `pols` polarisations, with nchan channels per
+ * subband (2*nchan-point transforms) and integrations of tint_s seconds.
+ * stations 1..256, subbands*pols 1..32, pols 1 or 2, nchan a power of two in
+ * 4..8192, tint_s > 0.  *h receives the handle (NULL on failure).  Allocates
+ * host state only; device memory is allocated at the first corr_correlate*
+ * call. */
 int corr_create(corr_t **h, int stations, int subbands, int pols, int nchan, double tint_s);
 
 /* Sample rate per stream (Hz, default 32e6) and the code -> level table
@@ -120,6 +125,19 @@ int corr_set_precision(corr_t *h, int mode);
  * Only before the first correlate call (CORR_ESTATE). */
 enum { CORR_ROT_POST_F = 0, CORR_ROT_PRE_F = 1 };
 int corr_set_fringe_rotation(corr_t *h, int mode);
+
+/* Mark5B-style framed input (the paper, Sec. 2: RadioAstron recordings are
+ * converted to Mark5B).  With payload_bytes > 0 (a multiple of 16; Mark5B
+ * uses 10000) every station's pushed or attached bytes are frames of a
+ * 16-byte header and payload_bytes of payload; the payloads in frame order
+ * are the packed stream described at the top of this file.  A frame whose
+ * first header word (32-bit little-endian) is not the sync word 0xABADDEED
+ * is taken as lost: every block that reads a sample from it is not valid at
+ * that station.  Only whole frames count as data.  The library deframes new
+ * frames on the device before each correlate call (a copy of the payloads,
+ * held in device memory of its own).  0 (the default): plain packed bytes.
+ * Only before any samples are pushed or attached (CORR_ESTATE). */
+int corr_set_frame_format(corr_t *h, int payload_bytes);
 
 /* Which polarisation products the X step forms.  CORR_POL_PARALLEL (the
  * default): each polarisation with itself, V_ab^pp, output
@@ -170,9 +188,13 @@ int corr_set_stream_start(corr_t *h, int station, int64_t first_sample);
 /* Reserve device room for nbytes of a station's packed samples (optional). */
 int corr_reserve(corr_t *h, int station, size_t nbytes);
 
-/* Append packed bytes (host memory) to a station's stream.  nbytes must be a
- * multiple of 4.  The bytes are copied to the device before the call returns,
- * so the caller may reuse the buffer; pinned host memory copies fastest. */
+/* Append packed bytes (host memory) to a station's stream: the station's
+ * recorded samples as the paper's data path delivers them (Sec. 2: the
+ * RadioAstron recordings converted to Mark5B), in the packing described at
+ * the top of this file (or in frames, see corr_set_frame_format).  nbytes
+ * must be a multiple of 4.  The bytes are copied to the device before the
+ * call returns, so the caller may reuse the buffer; pinned host memory copies
+ * fastest. */
 int corr_push_samples(corr_t *h, int station, const void *bytes, size_t nbytes);
 
 /* Append packed bytes without waiting for the copy: the copy runs on the
@@ -208,9 +230,12 @@ int corr_attach_samples_host(corr_t *h, int station, const void *host_bytes, siz
  * then produced with those blocks marked invalid instead of CORR_EAGAIN. */
 int corr_flush(corr_t *h);
 
-/* Correlate the next integration and copy it to host memory.
- * out: nbl*subbands*pols*nchan complex64 (2 floats each); weights: nbl doubles
- * or NULL.  Returns CORR_EAGAIN (nothing consumed) when some station has not
+/* Correlate the next integration and copy it to host memory: steps 1-5 at
+ * the top of this file for every block of the integration -- the FX order of
+ * the paper's Abstract, with each station's delay taken from its delay-model
+ * polynomial (Sec. 2) -- and V_ab / (W_ab * N) at its end.
+ * out: nbl*subbands*pols*nchan complex64 (2 floats each; with both hands of
+ * two polarisations nbl*subbands*4*nchan); weights: nbl doubles or NULL.  Returns CORR_EAGAIN (nothing consumed) when some station has not
  * pushed the samples the integration needs and corr_flush was not called,
  * CORR_EEND after corr_flush when no station has data left.  Blocks until the
  * device work is done. */

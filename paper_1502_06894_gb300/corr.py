@@ -71,6 +71,7 @@ _SIGS = {
     "corr_set_pipeline": ([_H, C.c_int], C.c_int),
     "corr_set_fringe_rotation": ([_H, C.c_int], C.c_int),
     "corr_set_pol_products": ([_H, C.c_int], C.c_int),
+    "corr_set_frame_format": ([_H, C.c_int], C.c_int),
     "corr_set_delay_poly": ([_H, C.c_int, C.c_double, _P], C.c_int),
     "corr_set_stream_start": ([_H, C.c_int, C.c_int64], C.c_int),
     "corr_reserve": ([_H, C.c_int, C.c_size_t], C.c_int),
@@ -181,6 +182,9 @@ class Correlator:
 
     def set_fringe_rotation(self, mode: int):
         self._check(corr_set_fringe_rotation(self.h, int(mode)))
+
+    def set_frame_format(self, payload_bytes: int):
+        self._check(corr_set_frame_format(self.h, int(payload_bytes)))
 
     def set_pol_products(self, mode: int):
         self._check(corr_set_pol_products(self.h, int(mode)))
@@ -456,7 +460,10 @@ class Server:
         # registered before the worker can report on it
         self._jobs[key] = {"shape": (nbl, d.subbands, d.pols, d.nchan), "nint": int(integrations),
                            "keep": static_scan}
-        rc = corr_server_submit(self.h, C.byref(job), self._cb, C.c_void_p(key), C.byref(jid))
+        # no Python callback at all when nobody listens (results still reach
+        # the server's pinned host buffers every integration)
+        fn = self._cb if self.on_result is not None else RESULT_FN()  # RESULT_FN(): a NULL pointer
+        rc = corr_server_submit(self.h, C.byref(job), fn, C.c_void_p(key), C.byref(jid))
         if rc != CORR_OK:
             self._jobs.pop(key, None)
             raise CorrError(rc, "corr_server_submit")

@@ -39,6 +39,13 @@ struct Station {
   int64_t sample0 = 0;
   bool started = false;     // a push or attach happened
   std::vector<Seg> segs;
+  // framed input: the frames' payloads deframed on the device, and their
+  // sync flags (frames [0, nframes_done) so far)
+  uint8_t* pay = nullptr;
+  size_t pay_cap = 0;
+  uint8_t* fok = nullptr;
+  size_t fok_cap = 0;
+  int64_t nframes_done = 0;
   // asynchronous pushes not yet waited for by the compute stream: the byte
   // range of each piece and the event recorded after its copy
   struct Piece {
@@ -63,6 +70,7 @@ struct corr_s {
   int precision = CORR_PREC_FP32;
   int rotation = CORR_ROT_POST_F;
   int pol_products = CORR_POL_PARALLEL;
+  int payload = 0;  // bytes of payload per Mark5B-style frame, 0: plain packed bytes
   cudaStream_t own_stream = nullptr;
   cudaStream_t copy_stream[kCopyStreams] = {nullptr, nullptr};
   int copy_next = 0;
@@ -238,8 +246,16 @@ static int drain_pushes(corr_t* h) {
   return CORR_OK;
 }
 
+// Whole frames in a station's (framed) bytes.
+static int64_t station_frames(const corr_t* h, const Station& s) {
+  return h->payload > 0 ? (int64_t)(s.len / (size_t)(kFrameHeader + h->payload)) : 0;
+}
+
+// Sample-time groups a station's bytes hold (for framed input: those of the
+// whole frames' payloads).
 static int64_t station_groups(const corr_t* h, const Station& s) {
-  return (int64_t)((s.len * 4) / (size_t)h->G);
+  const size_t bytes = h->payload > 0 ? (size_t)station_frames(h, s) * h->payload : s.len;
+  return (int64_t)((bytes * 4) / (size_t)h->G);
 }
 
 static const uint8_t* station_ptr(const Station& s) { return s.attached ? s.ext : s.dbuf; }
@@ -475,6 +491,56 @@ static int prepare(corr_t* h) {
   return CORR_OK;
 }
 
+// Deframe every station's frames that arrived since the last call into its
+// payload buffer (grown as needed), with their sync flags.
+static int deframe_new(corr_t* h) {
+  for (Station& x : h->st) {
+    const int64_t nf = station_frames(h, x);
+    if (nf <= x.nframes_done) continue;
+    if (!x.pending.empty()) {  // asynchronous pushes: the frames must have landed
+      int rc = drain_pushes(h);
+      if (rc) return rc;
+    }
+    const size_t need_pay = (size_t)nf * h->payload, need_ok = (size_t)nf;
+    if (need_pay > x.pay_cap || need_ok > x.fok_cap) {
+      // the F step and a look-ahead delay evaluation may still read the old buffers
+      int rc = drop_lookahead(h);
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(h->stream), "sync before payload growth");
+      size_t cp = x.pay_cap ? x.pay_cap : ((size_t)1 << 20);
+      while (cp < need_pay) cp *= 2;
+      size_t co = x.fok_cap ? x.fok_cap : 4096;
+      while (co < need_ok) co *= 2;
+      uint8_t *np = nullptr, *no = nullptr;
+      if ((rc = dalloc(h, (void**)&np, cp, "frame payloads"))) return rc;
+      if ((rc = dalloc(h, (void**)&no, co, "frame flags"))) {
+        cudaFree(np);
+        return rc;
+      }
+      const size_t done_pay = (size_t)x.nframes_done * h->payload;
+      cudaError_t e = cudaSuccess;
+      if (done_pay) e = cudaMemcpyAsync(np, x.pay, done_pay, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess && x.nframes_done)
+        e = cudaMemcpyAsync(no, x.fok, (size_t)x.nframes_done, cudaMemcpyDeviceToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) {
+        cudaFree(np);
+        cudaFree(no);
+        return h->cuda_fail(e, "payload growth");
+      }
+      cudaFree(x.pay);
+      cudaFree(x.fok);
+      x.pay = np;
+      x.pay_cap = cp;
+      x.fok = no;
+      x.fok_cap = co;
+    }
+    CK(launch_deframe(station_ptr(x), h->payload, x.nframes_done, nf, x.pay, x.fok, h->stream), "deframe launch");
+    x.nframes_done = nf;
+  }
+  return CORR_OK;
+}
+
 static int upload_model(corr_t* h) {
   const int S = h->S;
   for (int s = 0; s < S; ++s)
@@ -499,6 +565,11 @@ static int upload_model(corr_t* h) {
     CK(cudaMemcpy(h->d_nu0, h->nu0.data(), sizeof(double) * h->nsub, cudaMemcpyHostToDevice), "nu0 H2D");
     h->polys_dirty = false;
   }
+  // framed input: deframe the frames that arrived since the last call
+  if (h->payload > 0) {
+    int rc2 = deframe_new(h);
+    if (rc2) return rc2;
+  }
   // station views: the pinned staging copy holds what the device has; copy
   // again only when a push or attach changed them
   std::vector<StationView> views(S);
@@ -511,6 +582,14 @@ static int upload_model(corr_t* h) {
     v.nwords = (int64_t)(x.len / 4);
     v.sample0 = x.sample0;
     v.ngroups = station_groups(h, x);
+    if (h->payload > 0) {  // the kernels read the deframed payload (device memory)
+      v.words = reinterpret_cast<const uint32_t*>(x.pay);
+      v.host = 0;
+      v.nwords = x.nframes_done * (int64_t)h->payload / 4;
+      v.payload = h->payload;
+      v.frame_ok = x.fok;
+      v.nframes = x.nframes_done;
+    }
   }
   if (h->views_valid && memcmp(views.data(), h->h_views, sizeof(StationView) * S) == 0) return CORR_OK;
   // the F step and a look-ahead delay evaluation may still read the old views
@@ -530,6 +609,7 @@ static DelayParams delay_params(corr_t* h, int64_t b0, int nb, int ld, int slot)
   p.S = h->S;
   p.nsub = h->nsub;
   p.N = h->N;
+  p.G = h->G;
   p.fs = h->fs;
   p.nseg = h->d_nseg;
   p.seg_t0 = h->d_seg_t0;
@@ -916,6 +996,16 @@ int corr_set_precision(corr_t* h, int mode) {
   return CORR_OK;
 }
 
+int corr_set_frame_format(corr_t* h, int payload_bytes) {
+  if (!h) return CORR_EINVAL;
+  if (payload_bytes < 0 || payload_bytes % 16)
+    return h->fail(CORR_EINVAL, "corr_set_frame_format: payload bytes must be 0 or a positive multiple of 16");
+  for (const Station& x : h->st)
+    if (x.started) return h->fail(CORR_ESTATE, "corr_set_frame_format: only before any samples are pushed or attached");
+  h->payload = payload_bytes;
+  return CORR_OK;
+}
+
 int corr_set_pol_products(corr_t* h, int mode) {
   if (!h) return CORR_EINVAL;
   if (mode != CORR_POL_PARALLEL && mode != CORR_POL_CROSS)
@@ -1200,6 +1290,7 @@ int corr_reset(corr_t* h) {
     } else {
       s.len = 0;
     }
+    s.nframes_done = 0;
     s.started = false;
   }
   h->flushed = false;
@@ -1231,6 +1322,8 @@ void corr_destroy(corr_t* h) {
   for (Station& s : h->st) {
     for (auto& pe : s.pending) cudaEventDestroy(pe.ev);
     cudaFree(s.dbuf);
+    cudaFree(s.pay);
+    cudaFree(s.fok);
   }
   for (auto& m : h->marks) {
     cudaEventDestroy(m.a);
@@ -1369,8 +1462,12 @@ int corr_device_bytes(corr_t* h, size_t* bytes) {
   int rc = work_layout(h, w);
   if (rc) return rc;
   size_t total = w.total();
-  for (const Station& x : h->st)
+  for (const Station& x : h->st) {
     if (!x.attached) total += x.cap;  // sample buffers the handle owns
+    if (h->payload > 0)               // deframed payloads and their flags
+      total += std::max(x.pay_cap, (size_t)station_frames(h, x) * h->payload) +
+               std::max(x.fok_cap, (size_t)station_frames(h, x));
+  }
   *bytes = total;
   return CORR_OK;
 }

@@ -18,7 +18,20 @@ struct StationView {
   int64_t sample0;   // station sample index of the first sample-time group
   int64_t ngroups;   // sample-time groups present (for validity)
   int host;          // 1: the words are pinned host memory read over the host link
+  // framed input (payload > 0): `words` is the concatenated payload of the
+  // frames present; frame_ok[f] says whether frame f carried its sync word
+  int payload;              // payload bytes per frame, 0 for plain input
+  const uint8_t* frame_ok;  // [nframes]
+  int64_t nframes;
 };
+
+// Mark5B-style frames: a 16-byte header (word 0 the sync word) and a payload.
+constexpr uint32_t kFrameSync = 0xABADDEEDu;
+constexpr int kFrameHeader = 16;
+// Copy the payloads of frames [f0, f1) of `raw` (frames of 16 + payload bytes)
+// to payload[f * payload], and their sync flags to frame_ok[f].
+cudaError_t launch_deframe(const uint8_t* raw, int payload, int64_t f0, int64_t f1, uint8_t* payload_out,
+                           uint8_t* frame_ok, cudaStream_t s);
 
 constexpr int kMaxStations = 256;
 constexpr int kMaxDevices = 64;
@@ -27,7 +40,7 @@ constexpr int kMaxSub = 64;
 
 // Delay-model inputs for the delay-block kernel.
 struct DelayParams {
-  int S, nsub, N;
+  int S, nsub, N, G;
   double fs;
   const int* nseg;          // [S]
   const double* seg_t0;     // [S][kMaxSegs]

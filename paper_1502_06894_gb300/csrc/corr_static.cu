@@ -168,6 +168,9 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
       vb.v[q].sample0 = d->first_sample[s];
       vb.v[q].ngroups = (int64_t)((d->nbytes[s] * 4) / (size_t)G);
       vb.v[q].host = 0;
+      vb.v[q].payload = 0;
+      vb.v[q].frame_ok = nullptr;
+      vb.v[q].nframes = 0;
     }
     k_static_views<<<1, kViewsPerLaunch, 0, st>>>(vb, n, (StationView*)(base + o_views) + s0);
     e = cudaGetLastError();
@@ -196,6 +199,7 @@ extern "C" int corr_correlate_static(const corr_scan_desc* d, int64_t integratio
   dp.S = S;
   dp.nsub = nsub;
   dp.N = N;
+  dp.G = G;
   dp.fs = d->fs_hz;
   dp.nseg = (const int*)(base + o_nseg);
   dp.seg_t0 = (const double*)(base + o_t0);

@@ -45,7 +45,13 @@ __global__ void k_delay_blocks(DelayParams p) {
   const int64_t start = b * (int64_t)N + n;
   const StationView v = p.st[s];
   const int64_t rel = start - v.sample0;
-  const bool ok = covered && rel >= 0 && rel + N <= v.ngroups;
+  bool ok = covered && rel >= 0 && rel + N <= v.ngroups;
+  if (ok && v.payload > 0) {
+    // framed input: every frame holding a byte of the window must be valid
+    const int G = p.G;
+    const int64_t qa = (2 * rel * G) >> 3, qb = (2 * (rel + N) * G - 1) >> 3;
+    for (int64_t f = qa / v.payload; f <= qb / v.payload && ok; ++f) ok = f < v.nframes && v.frame_ok[f] != 0;
+  }
   const size_t o = (size_t)s * p.ld + i;
   p.start[o] = start;
   p.valid[o] = ok ? 1 : 0;
@@ -91,6 +97,32 @@ __global__ void k_delay_blocks(DelayParams p) {
     atomicMin(&p.max_end[3 * s + 1], (unsigned long long)rel + off);
     if (ok) atomicAdd(&p.max_end[3 * s + 2], 1ull);
   }
+}
+
+// Deframe: one CTA row per frame; the payload moves in 16-byte pieces (the
+// payload and the frame length are multiples of 16 bytes).
+__global__ void k_deframe(const uint8_t* __restrict__ raw, int payload, int64_t f0, int64_t f1,
+                          uint8_t* __restrict__ out, uint8_t* __restrict__ frame_ok) {
+  const int64_t f = f0 + blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+  if (f >= f1) return;
+  const uint8_t* fr = raw + f * (int64_t)(kFrameHeader + payload);
+  const uint4* src = reinterpret_cast<const uint4*>(fr + kFrameHeader);
+  uint4* dst = reinterpret_cast<uint4*>(out + f * (int64_t)payload);
+  const int n16 = payload / 16;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += gridDim.x * blockDim.x) dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) frame_ok[f] = *reinterpret_cast<const uint32_t*>(fr) == kFrameSync;
+}
+
+cudaError_t launch_deframe(const uint8_t* raw, int payload, int64_t f0, int64_t f1, uint8_t* payload_out,
+                           uint8_t* frame_ok, cudaStream_t s) {
+  if (f1 <= f0) return cudaSuccess;
+  const int64_t nf = f1 - f0;
+  const int n16 = payload / 16;
+  const unsigned gx = (unsigned)((n16 + 255) / 256 < 8 ? (n16 + 255) / 256 : 8);
+  const unsigned gy = (unsigned)(nf < 65535 ? nf : 65535);
+  const unsigned gz = (unsigned)((nf + gy - 1) / gy);
+  k_deframe<<<dim3(gx, gy, gz), 256, 0, s>>>(raw, payload, f0, f1, payload_out, frame_ok);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_delay_blocks(const DelayParams& p, cudaStream_t s) {

@@ -118,14 +118,29 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
   for (int u = 0; u < PER; ++u) {
     const int j = t + u * T;
     const int k = j & (NS - 1);
+    // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{TWS k r L/(NS R)} (TWS = N / L:
+    // 2 for the real transform packed into L = N/2 points, 1 for the complex
+    // N-point transform of the pre-F rotation).  For the last pass (NS R = L)
+    // from the shared table s_twl[r NS + k] when given; otherwise the powers
+    // W^k, W^2k, W^4k, ... come from the global table and W^{kr} is their
+    // product over the bits of r (at most log2 R - 1 multiplications deep),
+    // which keeps the memory pipeline, the bottleneck of the large
+    // transforms, to log2 R loads per butterfly group
+    if (NS * R == L && s_twl) {
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{TWS k r L/(NS R)} (TWS = N / L:
-      // 2 for the real transform packed into L = N/2 points, 1 for the complex
-      // N-point transform of the pre-F rotation); for the last pass (NS R = L)
-      // from the shared table s_twl[r NS + k] when given
-      const float2 w = (NS * R == L && s_twl) ? s_twl[r * NS + k] : __ldg(&twN[TWS * k * r * (L / (NS * R))]);
-      v[u][r] = cmul(v[u][r], w);
+      for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], s_twl[r * NS + k]);
+    } else {
+      constexpr int LOGR = ilog2c(R);
+      float2 wp[LOGR];
+#pragma unroll
+      for (int i = 0; i < LOGR; ++i) wp[i] = __ldg(&twN[TWS * k * (1 << i) * (L / (NS * R))]);
+      float2 w[R];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const int hb = ilog2c(r);  // r's highest bit (compile time after unrolling)
+        w[r] = (r == (1 << hb)) ? wp[hb] : cmul(w[r - (1 << hb)], wp[hb]);
+        v[u][r] = cmul(v[u][r], w[r]);
+      }
     }
     dft_reg<R>(v[u]);
     const int idxD = (j / NS) * NS * R + k;
