@@ -11,7 +11,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
-TOL_FP16 = 1.5e-3
+TOL_FP16 = 1e-3
 
 
 @pytest.fixture(scope="module")

@@ -14,7 +14,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1.5e-3, 2: 8e-2}
+TOL = {0: 1e-5, 1: 1e-3, 2: 8e-2}
 
 
 @pytest.fixture(scope="module")

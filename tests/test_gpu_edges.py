@@ -21,7 +21,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1.5e-3, 2: 8e-2}  # FP32, FP16 tensor cores, FP8 tensor cores
+TOL = {0: 1e-5, 1: 1e-3, 2: 8e-2}  # FP32, FP16 tensor cores, FP8 tensor cores
 
 
 @pytest.fixture(scope="module")

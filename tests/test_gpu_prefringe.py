@@ -19,7 +19,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-5, 1: 1.5e-3, 2: 8e-2}
+TOL = {0: 1e-5, 1: 1e-3, 2: 8e-2}
 ETA = 0.8825  # 2-bit efficiency at +-0.98 sigma with levels 1 / 3.336 (pinned on the CPU)
 
 

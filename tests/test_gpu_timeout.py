@@ -41,7 +41,7 @@ def rel_rms_max(v, ref):
     return float(np.max(np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=(1, 2)) / np.sum(np.abs(ref) ** 2, axis=(1, 2)))))
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1.5e-3), (2, 8e-2)])
+@pytest.mark.parametrize("precision,tol", [(0, 1e-5), (1, 1e-3), (2, 8e-2)])
 def test_timeout_reported_until_reset(corr, scan, precision, tol):
     sc, streams, ref, wref = scan
     c = corr.from_scan(sc, streams)
