@@ -121,6 +121,63 @@ __device__ __forceinline__ void load_pair_g(const StationView& sv, int64_t rel, 
   }
 }
 
+// Channels k (low half) and L - k (high half) of one block as one 8-byte
+// slot: two FP16 complex values, or two E4M3 complex values in the low 4 bytes.
+template <bool FP8>
+__device__ __forceinline__ void put_pair(float2* slot, float2 a, float2 b, float scale) {
+  if constexpr (FP8) {
+    *reinterpret_cast<uint32_t*>(slot) = fp8x2(a.x * scale, a.y * scale) | (fp8x2(b.x * scale, b.y * scale) << 16);
+  } else {
+    const __half2 ha = __floats2half2_rn(a.x * scale, a.y * scale), hb = __floats2half2_rn(b.x * scale, b.y * scale);
+    *reinterpret_cast<uint2*>(slot) = make_uint2(*reinterpret_cast<const uint32_t*>(&ha),
+                                                 *reinterpret_cast<const uint32_t*>(&hb));
+  }
+}
+
+// Byte address of row r's 16-byte chunk kc in the tile of (stream jo, channel ch, K tile kt).
+__device__ __forceinline__ unsigned char* chunk_at(const TcTiles& o, int S, int s, int jo, int kt, int kc, int ch,
+                                                   int reim) {
+  const int sl = ch / o.W;
+  const int cw = ch - sl * o.W;
+  const int tg = cw / o.cpt;
+  const int cl = cw - tg * o.cpt;
+  const int r = (cl * S + s) * 2 + reim;
+  unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+  return tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4);
+}
+
+// The FP16 values of channel ch (half h of each slot) in 8 consecutive
+// blocks: one 16-byte chunk for Re and one for Im.
+__device__ __forceinline__ void put_chunk16(const TcTiles& o, int S, int s, int jo, int kt, int kc, int ch,
+                                            const uint2 (&w)[8], int h) {
+  uint32_t re[4], im[4];
+#pragma unroll
+  for (int e = 0; e < 8; e += 2) {
+    const uint32_t a = h ? w[e].y : w[e].x, b = h ? w[e + 1].y : w[e + 1].x;  // (Re, Im) as two halves
+    re[e / 2] = __byte_perm(a, b, 0x5410);
+    im[e / 2] = __byte_perm(a, b, 0x7632);
+  }
+  *reinterpret_cast<uint4*>(chunk_at(o, S, s, jo, kt, kc, ch, 0)) = make_uint4(re[0], re[1], re[2], re[3]);
+  *reinterpret_cast<uint4*>(chunk_at(o, S, s, jo, kt, kc, ch, 1)) = make_uint4(im[0], im[1], im[2], im[3]);
+}
+
+// The same for E4M3: 8 blocks x (Re byte, Im byte) -> 8 Re bytes and 8 Im
+// bytes, the half chunk khalf of the K range's 16-byte chunk.
+__device__ __forceinline__ void put_chunk8(const TcTiles& o, int S, int s, int jo, int kt, int kc, int khalf, int ch,
+                                           const uint32_t (&w)[8], int h) {
+  uint32_t v[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) v[e] = h ? (w[e] >> 16) : (w[e] & 0xffffu);
+  const uint32_t r01 = __byte_perm(v[0], v[1], 0x0040), r23 = __byte_perm(v[2], v[3], 0x0040);
+  const uint32_t r45 = __byte_perm(v[4], v[5], 0x0040), r67 = __byte_perm(v[6], v[7], 0x0040);
+  const uint32_t i01 = __byte_perm(v[0], v[1], 0x0051), i23 = __byte_perm(v[2], v[3], 0x0051);
+  const uint32_t i45 = __byte_perm(v[4], v[5], 0x0051), i67 = __byte_perm(v[6], v[7], 0x0051);
+  *reinterpret_cast<uint2*>(chunk_at(o, S, s, jo, kt, kc, ch, 0) + khalf) =
+      make_uint2(__byte_perm(r01, r23, 0x5410), __byte_perm(r45, r67, 0x5410));
+  *reinterpret_cast<uint2*>(chunk_at(o, S, s, jo, kt, kc, ch, 1) + khalf) =
+      make_uint2(__byte_perm(i01, i23, 0x5410), __byte_perm(i45, i67, 0x5410));
+}
+
 template <int L, int GC, bool FP8>
 __global__ void __launch_bounds__(Groups<L>::T * GroupsTC<L>::NGRP, MinBlocksTC<L>::v)
 k_fstage_tc(FParams p, TcTiles o) {
@@ -133,7 +190,6 @@ k_fstage_tc(FParams p, TcTiles o) {
   constexpr int R0 = P::R0;
   constexpr int PER0 = L / R0 / T;
   constexpr int HALF = L / 2;
-  constexpr int QN = HALF / T + 1;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* fbuf_all = reinterpret_cast<float2*>(smem_raw);
@@ -191,103 +247,62 @@ k_fstage_tc(FParams p, TcTiles o) {
       if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0>(fbuf, t, grp, p.twN);
     }
 
-    // ---- real split + rotation into registers, then FP16 / FP8 into the group's buffer ----
+    // ---- real split + rotation; the FP16 (E4M3) values of channels k and
+    //      L - k go into the float2 slot of Z[k]: only this thread reads
+    //      that slot (and the one of Z[L - k]), so it writes without a
+    //      barrier and holds nothing in registers ----
     constexpr int QF = HALF / T;  // k = t + qT < HALF for q < QF; k = HALF is thread 0's extra
-    float2 xa[QN], xb[QN];
-#pragma unroll
-    for (int q = 0; q < QN; ++q) {
-      xa[q] = make_float2(0.f, 0.f);
-      xb[q] = make_float2(0.f, 0.f);
-    }
     if (ok) {
       const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
       float2 z = cis_turns(fmaf((float)t, delta, phi));
       float2 y = cis_turns(fmaf((float)(L - t), delta, phi));
       float cm1, sn;
       walk_step((float)T * delta, cm1, sn);
-#pragma unroll
+      SplitTw<L, T> tw(s_tw, p.twN, t);
+#pragma unroll 4
       for (int q = 0; q < QF; ++q) {
         const int k = t + q * T;
         float2 Xa, Xb;
-        split_pair<L, R0>(fbuf, s_tw, p.twN, k, (L - k) & (L - 1), Xa, Xb);
-        xa[q] = cmul(Xa, z);
-        xb[q] = cmul(Xb, y);
+        split_pair<L, R0>(fbuf, tw.get(s_tw, k), k, (L - k) & (L - 1), Xa, Xb);
+        put_pair<FP8>(fbuf + padp<R0>(k), cmul(Xa, z), cmul(Xb, y), o.scale);
         z = walk(z, cm1, sn);
         y = walk(y, cm1, -sn);
+        tw.next();
       }
       if (t == 0) {
         float2 Xa, Xb;
-        split_pair<L, R0>(fbuf, s_tw, p.twN, HALF, HALF, Xa, Xb);
-        xa[QF] = cmul(Xa, z);
-      }
-    }
-    gsync<T>(grp);
-    if constexpr (FP8) {
-      uint16_t* x8 = reinterpret_cast<uint16_t*>(fbuf);
-#pragma unroll
-      for (int q = 0; q < QN; ++q) {
-        const int k = t + q * T;
-        if (k <= HALF) {
-          const int km = (L - k) & (L - 1);
-          x8[k] = (uint16_t)fp8x2(xa[q].x * o.scale, xa[q].y * o.scale);
-          if (k != 0 && k != HALF) x8[km] = (uint16_t)fp8x2(xb[q].x * o.scale, xb[q].y * o.scale);
-        }
+        split_pair<L, R0>(fbuf, make_float2(0.f, -1.f), HALF, HALF, Xa, Xb);
+        put_pair<FP8>(fbuf + padp<R0>(HALF), cmul(Xa, z), make_float2(0.f, 0.f), o.scale);
       }
     } else {
-      __half2* xh = reinterpret_cast<__half2*>(fbuf);
-#pragma unroll
-      for (int q = 0; q < QN; ++q) {
-        const int k = t + q * T;
-        if (k <= HALF) {
-          const int km = (L - k) & (L - 1);
-          xh[k] = __floats2half2_rn(xa[q].x * o.scale, xa[q].y * o.scale);
-          if (k != 0 && k != HALF) xh[km] = __floats2half2_rn(xb[q].x * o.scale, xb[q].y * o.scale);
-        }
-      }
+      const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll 4
+      for (int q = 0; q < QF; ++q) put_pair<FP8>(fbuf + padp<R0>(t + q * T), zero, zero, o.scale);
+      if (t == 0) put_pair<FP8>(fbuf + padp<R0>(HALF), zero, zero, o.scale);
     }
     __syncthreads();
 
-    // ---- corner turn: 8 blocks of (stream, channel, Re/Im) -> one 16-byte chunk ----
-    for (int it = tid; it < SPR * L; it += NGRP * T) {
-      const int ss = it / L;
-      const int k = it - ss * L;
+    // ---- corner turn: for each channel pair (c, L - c) the 8 blocks' slots
+    //      become, per channel and Re/Im, one 16-byte chunk (FP8: 8 bytes) ----
+    for (int it = tid; it < SPR * (HALF + 1); it += NGRP * T) {
+      const int ss = it / (HALF + 1);
+      const int c = it - ss * (HALF + 1);
       const int jo = r0 + ss;
       if (jo >= G) continue;
-      const int sl = k / o.W;
-      const int cw = k - sl * o.W;
-      const int tg = cw / o.cpt;
-      const int cl = cw - tg * o.cpt;
-      const int r = (cl * p.S + s) * 2;
-      unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+      const float2* slot0 = fbuf_all + (size_t)(ss * 8) * BUF + padp<R0>(c);
       if constexpr (FP8) {
-        // 8 blocks x (Re byte, Im byte) -> 8 Re bytes and 8 Im bytes
         uint32_t w[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) w[e] = reinterpret_cast<const uint16_t*>(fbuf_all + (ss * 8 + e) * BUF)[k];
-        const uint32_t r01 = __byte_perm(w[0], w[1], 0x0040), r23 = __byte_perm(w[2], w[3], 0x0040);
-        const uint32_t r45 = __byte_perm(w[4], w[5], 0x0040), r67 = __byte_perm(w[6], w[7], 0x0040);
-        const uint32_t i01 = __byte_perm(w[0], w[1], 0x0051), i23 = __byte_perm(w[2], w[3], 0x0051);
-        const uint32_t i45 = __byte_perm(w[4], w[5], 0x0051), i67 = __byte_perm(w[6], w[7], 0x0051);
-        *reinterpret_cast<uint2*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4) + khalf) =
-            make_uint2(__byte_perm(r01, r23, 0x5410), __byte_perm(r45, r67, 0x5410));
-        const int r1 = r + 1;
-        *reinterpret_cast<uint2*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4) + khalf) =
-            make_uint2(__byte_perm(i01, i23, 0x5410), __byte_perm(i45, i67, 0x5410));
-        continue;
-      }
-      uint32_t re[4], im[4];
+        for (int e = 0; e < 8; ++e) w[e] = *reinterpret_cast<const uint32_t*>(slot0 + e * BUF);
+        put_chunk8(o, p.S, s, jo, kt, kc, khalf, c, w, 0);
+        if (c != 0 && c != HALF) put_chunk8(o, p.S, s, jo, kt, kc, khalf, L - c, w, 1);
+      } else {
+        uint2 w[8];
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        const __half2 a = reinterpret_cast<const __half2*>(fbuf_all + (ss * 8 + e) * BUF)[k];
-        const __half2 b = reinterpret_cast<const __half2*>(fbuf_all + (ss * 8 + e + 1) * BUF)[k];
-        re[e / 2] = (uint32_t)__half_as_ushort(__low2half(a)) | ((uint32_t)__half_as_ushort(__low2half(b)) << 16);
-        im[e / 2] = (uint32_t)__half_as_ushort(__high2half(a)) | ((uint32_t)__half_as_ushort(__high2half(b)) << 16);
+        for (int e = 0; e < 8; ++e) w[e] = *reinterpret_cast<const uint2*>(slot0 + e * BUF);
+        put_chunk16(o, p.S, s, jo, kt, kc, c, w, 0);
+        if (c != 0 && c != HALF) put_chunk16(o, p.S, s, jo, kt, kc, L - c, w, 1);
       }
-      *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) =
-          make_uint4(re[0], re[1], re[2], re[3]);
-      const int r1 = r + 1;
-      *reinterpret_cast<uint4*>(tile + (r1 >> 3) * 1024 + (r1 & 7) * 128 + ((kc ^ (r1 & 7)) << 4)) =
-          make_uint4(im[0], im[1], im[2], im[3]);
     }
     __syncthreads();
   }

@@ -19,15 +19,19 @@ __device__ __forceinline__ uint32_t fp8x2(float re, float im) {
 }
 
 
-static __constant__ float2 c_w32[32];  // exp(-2 pi i m / 32)
+static __constant__ float2 c_w32[32];   // exp(-2 pi i m / 32)
+static __constant__ float2 c_w32n[32];  // (-Im, Im) of the same, the second operand of a packed product
 
 static cudaError_t init_w32() {
-  float2 h[32];
+  float2 h[32], hn[32];
   for (int m = 0; m < 32; ++m) {
     double a = -2.0 * 3.14159265358979323846 * (double)m / 32.0;
     h[m] = make_float2((float)cos(a), (float)sin(a));
+    hn[m] = make_float2(-h[m].y, h[m].y);
   }
-  return cudaMemcpyToSymbol(c_w32, h, sizeof(h));
+  cudaError_t e = cudaMemcpyToSymbol(c_w32, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_w32n, hn, sizeof(hn));
 }
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
@@ -37,8 +41,25 @@ __host__ __device__ constexpr int bitrevc(int x, int bits) {
   return r;
 }
 
+// Complex arithmetic on packed FP32 pairs: one f32x2 instruction (add, mul
+// or fma) computes both parts of a complex value with the rounding of two
+// scalar instructions, which halves the instructions of the FFT butterflies
+// and products (the F kernels are bound by instruction issue); the swapped
+// and broadcast operands below are operand selections, not extra moves.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 swp(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+
+// a b = (a.x b.x - a.y b.y, a.y b.x + a.x b.y) = a (b.x, b.x) + swap(a) (-b.y, b.y)
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  return f2fma(swp(a), make_float2(-b.y, b.y), f2mul(a, bc(b.x)));
+}
+// a W_32^m, the second operand pair read ready-made from c_w32n
+__device__ __forceinline__ float2 cmul_w32(float2 a, int m) {
+  return f2fma(swp(a), c_w32n[m], f2mul(a, bc(c_w32[m].x)));
 }
 
 // Shared FFT buffers insert one padding element after every P elements (P =
@@ -48,7 +69,8 @@ template <int P>
 __device__ __forceinline__ int padp(int i) { return i + (i >> ilog2c(P)); }
 
 // In-register DFT of R points (R <= 32): radix-2 decimation in frequency,
-// natural-order input, output permuted back to natural order.
+// natural-order input, output permuted back to natural order.  Butterflies
+// with the twiddle -i rotate the difference by a swap and a sign pair.
 template <int R>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   constexpr int LOG = ilog2c(R);
@@ -60,15 +82,15 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 #pragma unroll
       for (int k = 0; k < half; ++k) {
         const float2 a = v[i + k], b = v[i + k + half];
-        v[i + k] = make_float2(a.x + b.x, a.y + b.y);
-        const float2 d = make_float2(a.x - b.x, a.y - b.y);
+        v[i + k] = f2add(a, b);
+        const float2 d = f2sub(a, b);
         const int m = k * (32 / (2 * half));  // W_{2 half}^k = W_32^m
         if (m == 0)
           v[i + k + half] = d;
         else if (m == 8)
-          v[i + k + half] = make_float2(d.y, -d.x);
+          v[i + k + half] = f2mul(swp(d), make_float2(1.f, -1.f));  // -i d
         else
-          v[i + k + half] = cmul(d, c_w32[m]);
+          v[i + k + half] = cmul_w32(d, m);
       }
     }
   }
@@ -97,15 +119,52 @@ __device__ __forceinline__ void gsync(int grp) {
   }
 }
 
+// v[r] *= W^{kr} for r = 1..R-1 from wp[i] = W^{k 2^i}: W^{kr} is wp of r's
+// highest bit times W^{k(r - that bit)} (indices fixed at compile time, so
+// every value stays in registers).
+template <int R, int LOGR, int r = 1>
+__device__ __forceinline__ void twiddle_products(float2 (&v)[R], float2 (&w)[R], const float2 (&wp)[LOGR]) {
+  if constexpr (r < R) {
+    constexpr int hb = ilog2c(r);
+    if constexpr (r == (1 << hb))
+      w[r] = wp[hb];
+    else
+      w[r] = cmul(w[r - (1 << hb)], wp[hb]);
+    v[r] = cmul(v[r], w[r]);
+    twiddle_products<R, LOGR, r + 1>(v, w, wp);
+  }
+}
+
 // A later Stockham pass: read R points per butterfly group, twiddle, DFT,
 // write back in place (all reads of the group finish before any write).
+// W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{TWS k r L/(NS R)} (TWS = N / L:
+// 2 for the real transform packed into L = N/2 points, 1 for the complex
+// N-point transform of the pre-F rotation).  For the last pass (NS R = L)
+// from the shared table s_twl[r NS + k] when given; otherwise the powers
+// W^k, W^2k, W^4k, ... come from the global table and W^{kr} is their
+// product over the bits of r (at most log2 R - 1 multiplications deep),
+// which keeps the memory pipeline, the bottleneck of the large transforms,
+// to log2 R loads per butterfly group.  Those loads depend on the thread
+// only, so they are issued first and their latency passes while the group
+// reads its points and waits at the barrier.
 template <int L, int R, int NS, int T, int P, int TWS = 2>
 __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, int grp,
                                               const float2* __restrict__ twN,
                                               const float2* __restrict__ s_twl = nullptr) {
   constexpr int GROUPS = L / R;
   constexpr int PER = GROUPS / T;
+  constexpr int LOGR = ilog2c(R);
   static_assert(PER >= 1 && GROUPS % T == 0, "bad FFT plan");
+  const bool tab = NS * R == L && s_twl != nullptr;
+  float2 wp[PER][LOGR];
+  if (!tab) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int k = (t + u * T) & (NS - 1);
+#pragma unroll
+      for (int i = 0; i < LOGR; ++i) wp[u][i] = __ldg(&twN[TWS * k * (1 << i) * (L / (NS * R))]);
+    }
+  }
   float2 v[PER][R];
 #pragma unroll
   for (int u = 0; u < PER; ++u) {
@@ -118,29 +177,12 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
   for (int u = 0; u < PER; ++u) {
     const int j = t + u * T;
     const int k = j & (NS - 1);
-    // W_{NS R}^{k r} = W_L^{k r L/(NS R)} = W_N^{TWS k r L/(NS R)} (TWS = N / L:
-    // 2 for the real transform packed into L = N/2 points, 1 for the complex
-    // N-point transform of the pre-F rotation).  For the last pass (NS R = L)
-    // from the shared table s_twl[r NS + k] when given; otherwise the powers
-    // W^k, W^2k, W^4k, ... come from the global table and W^{kr} is their
-    // product over the bits of r (at most log2 R - 1 multiplications deep),
-    // which keeps the memory pipeline, the bottleneck of the large
-    // transforms, to log2 R loads per butterfly group
-    if (NS * R == L && s_twl) {
+    if (tab) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], s_twl[r * NS + k]);
     } else {
-      constexpr int LOGR = ilog2c(R);
-      float2 wp[LOGR];
-#pragma unroll
-      for (int i = 0; i < LOGR; ++i) wp[i] = __ldg(&twN[TWS * k * (1 << i) * (L / (NS * R))]);
       float2 w[R];
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const int hb = ilog2c(r);  // r's highest bit (compile time after unrolling)
-        w[r] = (r == (1 << hb)) ? wp[hb] : cmul(w[r - (1 << hb)], wp[hb]);
-        v[u][r] = cmul(v[u][r], w[r]);
-      }
+      twiddle_products<R, LOGR>(v[u], w, wp[u]);
     }
     dft_reg<R>(v[u]);
     const int idxD = (j / NS) * NS * R + k;
@@ -162,15 +204,16 @@ template <> struct Plan<256>  { static constexpr int R0 = 16, R1 = 16, R2 = 1, T
 template <> struct Plan<512>  { static constexpr int R0 = 32, R1 = 16, R2 = 1, T = 16; };
 template <> struct Plan<1024> { static constexpr int R0 = 32, R1 = 32, R2 = 1, T = 32; };
 template <> struct Plan<2048> { static constexpr int R0 = 16, R1 = 16, R2 = 8, T = 128; };
-template <> struct Plan<4096> { static constexpr int R0 = 16, R1 = 16, R2 = 16, T = 128; };
+template <> struct Plan<4096> { static constexpr int R0 = 16, R1 = 16, R2 = 16, T = 256; };
 template <> struct Plan<8192> { static constexpr int R0 = 32, R1 = 16, R2 = 16, T = 256; };
 
 template <int L> struct Groups {
   static constexpr int T = Plan<L>::T;
   // 256 threads per CTA (64 one-thread transforms for the smallest sizes);
   // 4096-point complex transforms (8192-sample blocks) run four independent
-  // 128-thread transforms per CTA, so that barriers stay within a transform
-  // and four of them are in flight per SM
+  // 256-thread transforms per CTA of 1024 threads, so that barriers stay
+  // within a transform, four of them are in flight per SM and 32 warps hide
+  // the latency of the twiddle loads
   static constexpr int NGRP = T == 1 ? 64 : (L == 4096 ? 4 : 256 / T);
 };
 
@@ -219,17 +262,41 @@ template <int L> struct LastRadix {
 // transform of the halved samples, so E = Z[k] + conj Z[L-k] and
 // O = -i (Z[k] - conj Z[L-k]) carry the split's factor 1/2.
 template <int L, int R0>
-__device__ __forceinline__ void split_pair(const float2* __restrict__ fbuf, const float2* __restrict__ s_tw,
-                                           const float2* __restrict__ twN, int k, int km, float2& Xa, float2& Xb) {
+__device__ __forceinline__ void split_pair(const float2* __restrict__ fbuf, float2 w, int k, int km, float2& Xa,
+                                           float2& Xb) {
   const float2 Zk = fbuf[padp<R0>(k)];
   const float2 Zm = fbuf[padp<R0>(km)];
-  const float2 E = make_float2(Zk.x + Zm.x, Zk.y - Zm.y);
-  const float2 O = make_float2(Zk.y + Zm.y, Zm.x - Zk.x);
-  const float2 w = Tw<L>::on ? s_tw[L + k] : __ldg(&twN[k]);
-  const float2 WO = make_float2(w.x * O.x - w.y * O.y, w.x * O.y + w.y * O.x);
-  Xa = make_float2(E.x + WO.x, E.y + WO.y);
-  Xb = make_float2(E.x - WO.x, WO.y - E.y);
+  const float2 pm = make_float2(1.f, -1.f), mp = make_float2(-1.f, 1.f);
+  const float2 E = f2fma(Zm, pm, Zk);             // (Zk.x + Zm.x, Zk.y - Zm.y)
+  const float2 Ec = f2fma(Zk, pm, Zm);            // conj E
+  const float2 O = f2fma(swp(Zk), pm, swp(Zm));   // (Zk.y + Zm.y, Zm.x - Zk.x)
+  const float2 WO = cmul(O, w);
+  Xa = f2add(E, WO);
+  Xb = f2fma(WO, mp, Ec);                         // (E.x - WO.x, WO.y - E.y)
 }
+
+// The split's twiddles W_N^k along a thread's channels k = t + qT: from the
+// shared table for N <= 2048; above, W_N^t from the global table times
+// W_N^{qT} by a walk (one product per channel instead of a global load
+// whose latency the large transforms cannot hide; QF <= 16 steps add a few
+// ulp).
+template <int L, int T>
+struct SplitTw {
+  float2 w, step;
+  __device__ __forceinline__ SplitTw(const float2* __restrict__ s_tw, const float2* __restrict__ twN, int t) {
+    if constexpr (!Tw<L>::on) {
+      w = __ldg(&twN[t]);
+      step = __ldg(&twN[T]);
+    }
+  }
+  __device__ __forceinline__ float2 get(const float2* __restrict__ s_tw, int k) const {
+    if constexpr (Tw<L>::on) return s_tw[L + k];
+    else return w;
+  }
+  __device__ __forceinline__ void next() {
+    if constexpr (!Tw<L>::on) w = cmul(w, step);
+  }
+};
 
 // The rotation exp(+2 pi i (phi + k delta)) along a thread's channels
 // k = t + qT (and L - k): the first factor of each sequence comes from the
@@ -255,8 +322,9 @@ __device__ __forceinline__ void walk_step(float T_delta, float& cm1, float& sn) 
   cm1 = t2 * fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f);
 }
 
+// z + z (cm1 + i sn) = (z + z cm1) + swap(z) (-sn, sn)
 __device__ __forceinline__ float2 walk(float2 z, float cm1, float sn) {
-  return make_float2(fmaf(-z.y, sn, fmaf(z.x, cm1, z.x)), fmaf(z.x, sn, fmaf(z.y, cm1, z.y)));
+  return f2fma(swp(z), make_float2(-sn, sn), f2fma(z, bc(cm1), z));
 }
 
 template <int OUT>
@@ -293,20 +361,22 @@ __device__ __forceinline__ void split_rotate_store(const float2* __restrict__ fb
   float2 y = cis_turns(fmaf((float)(L - t), delta, phi));
   float cm1, sn;
   walk_step((float)T * delta, cm1, sn);
+  SplitTw<L, T> tw(s_tw, twN, t);
 #pragma unroll 4
   for (int q = 0; q < QF; ++q) {
     const int k = t + q * T;
     const int km = (L - k) & (L - 1);
     float2 Xa, Xb;
-    split_pair<L, R0>(fbuf, s_tw, twN, k, km, Xa, Xb);
+    split_pair<L, R0>(fbuf, tw.get(s_tw, k), k, km, Xa, Xb);
     store_spec<OUT>(out, obase + k, cmul(Xa, z), scale);
     if (k != 0) store_spec<OUT>(out, obase + km, cmul(Xb, y), scale);
     z = walk(z, cm1, sn);
     y = walk(y, cm1, -sn);
+    tw.next();
   }
   if (t == 0) {  // k = HALF: X[HALF] = E + W_N^{N/4} O; z has walked to it
     float2 Xa, Xb;
-    split_pair<L, R0>(fbuf, s_tw, twN, HALF, HALF, Xa, Xb);
+    split_pair<L, R0>(fbuf, make_float2(0.f, -1.f), HALF, HALF, Xa, Xb);
     store_spec<OUT>(out, obase + HALF, cmul(Xa, z), scale);
   }
 }
@@ -330,6 +400,11 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
                "l"(gsrc)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
                "l"(gsrc)
@@ -346,8 +421,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // The copy of slot sl starts at the 16-byte aligned word a0 = w0 & ~3; with
 // GC = 16 (one word per sample time) word w0 goes to an even index so that
 // every sample pair is one aligned 64-bit load (odd leads are copied word by
-// word, one word further on).  s_ok / s_boff receive each slot's validity
-// and the bit offset of its window from the slot's first word.
+// word, one word further on); with GC = 32 (two words per sample time, so
+// the lead is 0 or 2) word w0 goes to a 16-byte boundary so that a sample
+// pair is one aligned 16-byte load (a lead of 2 is copied in 8-byte pieces,
+// two words further on).  s_ok / s_boff receive each slot's validity and the
+// bit offset of its window from the slot's first word.
 template <int N, int GC>
 __device__ __forceinline__ void stage_windows(const FParams& p, const StationView& sv, int s, int G, int bb0,
                                               int nslots, uint32_t* wbuf, int wslot, int* s_ok, int* s_boff) {
@@ -366,7 +444,9 @@ __device__ __forceinline__ void stage_windows(const FParams& p, const StationVie
       if (w0 + nw > sv.nwords) nw = (int)(sv.nwords - w0);
     }
     const int lead = (int)(w0 & 3);
-    const int shift = (GC == 16) ? (lead & 1) : 0;
+    // GC = 16: the window's first word at an even index; GC = 32 (lead 0
+    // or 2): at a 16-byte boundary
+    const int shift = (GC == 16) ? (lead & 1) : (GC == 32 ? ((4 - lead) & 3) : 0);
     uint32_t* dst = wbuf + sl * wslot + shift;
     const int64_t a0 = w0 - lead;
     const int ntot = nw + lead;
@@ -396,7 +476,10 @@ __device__ __forceinline__ void stage_windows(const FParams& p, const StationVie
     } else {
       for (int q = tid; q < nvec; q += blockDim.x) {
         if (a0 + 4 * q + 4 <= sv.nwords) {
-          if (shift) {
+          if (shift == 2) {
+            cp_async8(dst + 4 * q, sv.words + a0 + 4 * q);
+            cp_async8(dst + 4 * q + 2, sv.words + a0 + 4 * q + 2);
+          } else if (shift) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) cp_async4(dst + 4 * q + u, sv.words + a0 + 4 * q + u);
           } else {
@@ -430,9 +513,12 @@ __device__ __forceinline__ void load_pair(const uint32_t* __restrict__ wsl, int 
     c0 = (w.x >> (2 * j)) & 3u;
     c1 = (w.y >> (2 * j)) & 3u;
   } else if constexpr (GC == 32) {
-    const int q = 4 * m + (j >> 4);
-    c0 = (wsl[q] >> (2 * (j & 15))) & 3u;
-    c1 = (wsl[q + 2] >> (2 * (j & 15))) & 3u;
+    // the staging put the window's first word at a 16-byte boundary: the
+    // four words of a sample pair are one aligned 16-byte load
+    const uint4 w = *reinterpret_cast<const uint4*>(wsl + 4 * m);
+    const bool hi = (j >> 4) != 0;
+    c0 = ((hi ? w.y : w.x) >> (2 * (j & 15))) & 3u;
+    c1 = ((hi ? w.w : w.z) >> (2 * (j & 15))) & 3u;
   } else {
     const int bit = boff + 2 * (2 * m * G + j);
     c0 = (wsl[bit >> 5] >> (bit & 31)) & 3u;
@@ -587,6 +673,10 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
       // (and shift) words
       const uint32_t* wsl = wcur + sl * wslot + (GC ? (boff >> 5) : 0);
       const int d = p.blk0 + bb0 + sl;
+      // the block's phase terms, loaded now so that their latency passes
+      // during the transform
+      const float delta = ok ? p.delta[(size_t)s * p.ld + d] : 0.f;
+      const float phi = (ok && !PRE) ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
 
       // ---- pass 0: unpack straight into registers (NS = 1, no twiddles);
       //      the transform of a block that is not valid is skipped ----
@@ -605,7 +695,7 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
               // s_lut16[c] = (l[c] / 2, l[0] / 2): twice its real part is level c
               const float lev = 2.0f * s_lut16[load_one<GC>(wsl, boff, G, m, j)].x;
               const float2 z = prerot(m, phi0, dph.x, dph.y);
-              v[u][r] = make_float2(lev * z.x, lev * z.y);
+              v[u][r] = f2mul(z, bc(lev));
             }
           }
         } else {
@@ -637,7 +727,6 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
       // ---- store (real split and post-F rotation, or the pre-F path's slope) ----
       if (active) {
         const int bb = bb0 + sl;
-        const float delta = ok ? p.delta[(size_t)s * p.ld + d] : 0.f;
         if constexpr (PRE) {
           constexpr int NCH = L / 2;
           const size_t obase = spec_row(p, j, bb, s) * (size_t)NCH;
@@ -648,7 +737,6 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
           else
             rotate_store_pre<L, T, R0, 0>(fbuf, t, ok, delta, p.out, obase, p.scale);
         } else {
-          const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
           const size_t obase = spec_row(p, j, bb, s) * (size_t)L;
           if (p.out_kind == 1)
             split_rotate_store<L, T, R0, 1>(fbuf, s_tw, p.twN, t, ok, phi, delta, p.out, obase, p.scale);
