@@ -251,19 +251,22 @@ def cpu_oracle_sample(scan, host_streams, seconds=CPU_SAMPLE_S, nj=None):
     return samples / dt, cores, dt, float(w.min()), vis[0]
 
 
-def sample_errors(corr, scan, host_streams, ref, seconds=CPU_SAMPLE_S, precisions=(0, 1, 2)):
+def sample_errors(corr, scan, host_streams, ref, seconds=CPU_SAMPLE_S, precisions=(0, 1, 2), units=(0, 2)):
     """Largest relative RMS per baseline of the GPU path (through the C ABI,
     host-pushed samples) against the oracle's visibilities `ref` of the same
-    sample, per precision: the measured error of the benchmarked workload."""
+    sample, per precision (FP16 / FP8 for each X unit: CORR_X_AUTO, and
+    CORR_X_TENSOR_CORES as "..._tensor_cores"): the measured error of the
+    benchmarked workload."""
     spi = int(round(scan.fs * seconds))
     nj = ref.shape[1]
     out = {}
-    for prec in precisions:
+    for prec, unit in [(p, u) for p in precisions for u in (units if p else (0,))]:
         c = corr.Correlator(scan.stations, scan.nsub, scan.npol, scan.nchan, seconds, fs=scan.fs)
         for sb, nu in enumerate(scan.nu0):
             if nu:
                 c.set_sky_freq(sb, nu)
         c.set_precision(prec)
+        c.set_x_unit(unit)
         for s, segs in enumerate(scan.polys):
             for g in segs:
                 c.set_delay_poly(s, g.t0, g.coeffs)
@@ -275,7 +278,7 @@ def sample_errors(corr, scan, host_streams, ref, seconds=CPU_SAMPLE_S, precision
         c.close()
         v = v.reshape(scan.nbl, scan.G, scan.nchan)[:, :nj]
         err = np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=(1, 2)) / np.sum(np.abs(ref) ** 2, axis=(1, 2)))
-        out[("fp32", "fp16", "fp8")[prec]] = float(err.max())
+        out[("fp32", "fp16", "fp8")[prec] + ("_tensor_cores" if unit == 2 else "")] = float(err.max())
     return out
 
 
@@ -498,7 +501,7 @@ def batch_leg(args, torch, corr, dev):
     """96 uneven scans (2-20 stations, 1-16 subbands, 1-2 pols, 128-8192
     channels, 0.5-30 s): all admitted at once and advanced one integration per
     step, every step one CUDA graph over all open scans, chunk lengths from
-    the autotuner, FP16 tensor-core X step.  Compared with the same scans one
+    the autotuner, FP16 spectra (X unit chosen per scan by CORR_X_AUTO).  Compared with the same scans one
     after another through corr_correlate_device (same precision and chunks),
     and with plain FP32 one after another at the library's default chunks.
     Samples come from a device-resident pool that every station reads at its
@@ -570,7 +573,7 @@ def serve_leg(args, torch, corr, dev):
     """The native continuous-batching server (corr_server_*): jobs drawn from
     the uneven scan mix arrive as a Poisson process and are admitted by HBM
     budget; every step advances all admitted jobs by one integration in one
-    CUDA graph (FP16 tensor-core X step) and copies every integration to
+    CUDA graph (FP16 spectra, X unit by CORR_X_AUTO) and copies every integration to
     pinned host memory.  A sweep over arrival rates gives offered load,
     served load and p50 / p99 latency (arrival to the last integration)."""
     import synth
@@ -597,7 +600,7 @@ def serve_leg(args, torch, corr, dev):
                         "1-16 subbands, 1-2 pols, 128-8192 channels, 0.5-30 s), HBM cap %.0f GB, reserve %.0f GB"
                         % (args.serve_window, args.hbm_cap / 1e9, args.hbm_reserve / 1e9),
             "unit": METRIC + " (offered, served); seconds (p50, p99)", "server": "native (corr_server_*)",
-            "precision": "FP16 tensor-core X step", "points": points,
+            "precision": "FP16 spectra, X unit by CORR_X_AUTO (CUDA cores up to 12 stations, tensor cores above)", "points": points,
             "named_window": "the named run (40 jobs/s for 120 s) offers several times the served load at every "
                             "rate above ~5 jobs/s, so its queue (and p99) grows without bound; the sweep shows "
                             "where the latency is the service time",
@@ -647,12 +650,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def device_leg(precision, pipeline=1):
-        """Time K steps of the device-resident path at one precision."""
+    def device_leg(precision, pipeline=1, unit=0):
+        """Time K steps of the device-resident path at one precision (and,
+        for FP16 / FP8, one X unit)."""
         c = corr.from_scan(scan, device_streams=dstreams)
         if args.chunk_blocks:
             c.set_chunk_blocks(args.chunk_blocks)
         c.set_precision(precision)
+        c.set_x_unit(unit)
         c.set_pipeline(pipeline)
         c.set_stream(stream.cuda_stream)
         c.flush()
@@ -694,12 +699,22 @@ def main():
     # time then is its own (with the overlap, F launches share SMs with X), so
     # this leg gives the per-kernel roofline
     ms_seq, prof, clocks_seq, _ = device_leg(corr.CORR_PREC_FP32, pipeline=0)
-    tc = None
+    # FP16 / FP8 spectra: the library's own choice of X unit (for 10
+    # stations the CUDA cores), and the tensor cores forced
+    # (each also with F and X in turn, for the per-kernel stage times)
+    tc = tc_mma = None
+    seq = {}
     if not args.no_tc:
         ms_tc, prof_tc, clocks_tc, _ = device_leg(corr.CORR_PREC_FP16_TC)
-    fp8 = None
+        ms_tcm, prof_tcm, clocks_tcm, _ = device_leg(corr.CORR_PREC_FP16_TC, unit=corr.CORR_X_TENSOR_CORES)
+        seq["tc"] = device_leg(corr.CORR_PREC_FP16_TC, pipeline=0)[:2]
+        seq["tc_mma"] = device_leg(corr.CORR_PREC_FP16_TC, pipeline=0, unit=corr.CORR_X_TENSOR_CORES)[:2]
+    fp8 = fp8_mma = None
     if not args.no_fp8:
         ms_f8, prof_f8, clocks_f8, _ = device_leg(corr.CORR_PREC_FP8_TC)
+        ms_f8m, prof_f8m, clocks_f8m, _ = device_leg(corr.CORR_PREC_FP8_TC, unit=corr.CORR_X_TENSOR_CORES)
+        seq["fp8"] = device_leg(corr.CORR_PREC_FP8_TC, pipeline=0)[:2]
+        seq["fp8_mma"] = device_leg(corr.CORR_PREC_FP8_TC, pipeline=0, unit=corr.CORR_X_TENSOR_CORES)[:2]
 
     # ---- roofline of the dominant kernel ----
     peak_hbm, peak_src = measured_peaks()
@@ -750,25 +765,33 @@ def main():
     roof["issue_frac"] = issue_frac(inst, t_launch, (clocks or {}).get("sm_mhz") or MAX_SM_MHZ)
     launches = prof_ovl["delay"][1] + prof_ovl["fstage"][1] + prof_ovl["xstage"][1] + 2 * prof_ovl["finalize"][1]
     x_tflops = x_flops / (x_ms / 1e3) / 1e12 if x_ms > 0 else None
-    def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound):
+    def tc_leg(ms_t, prof_t, clocks_t, dtype, elem_bytes, bound, unit, sq):
         xt_ms, xt_n = prof_t["xstage"]
         ft_ms, ft_n = prof_t["fstage"]
         # reduced-precision spectra: elem_bytes read per station-sample in the X step
         xt_bytes = steps * ss_step * elem_bytes
         return {"value": replica_value(sps, ws, ms_t), "unit": METRIC, "ms_per_step": ms_t, "dtype": dtype,
-                "error_bound_rel_rms": bound, "measured_rel_rms": None,
+                "x_unit": unit, "error_bound_rel_rms": bound, "measured_rel_rms": None,
                 "xstep_ms_per_step": xt_ms / steps, "fstage_ms_per_step": ft_ms / steps,
                 "xstep_tflops": x_flops / (xt_ms / 1e3) / 1e12 if xt_ms > 0 else None,
                 "xstep_hbm_gbs": xt_bytes / (xt_ms / 1e3) / 1e9 if xt_ms > 0 else None,
                 "xstep_vs_fp32_xstep": (x_ms / xt_ms) if xt_ms > 0 else None,
                 "stages": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
                            for k, v in prof_t.items()},
+                "sequential": {"ms_per_step": sq[0],
+                               "stages": {k: {"ms_per_step": v[0] / steps, "launches_per_step": v[1] / steps}
+                                          for k, v in sq[1].items()}},
                 "clocks": clocks_t}
 
+    auto_unit = "CUDA cores (CORR_X_AUTO: %d stations <= 12)" % S if S <= 12 else "tensor cores (CORR_X_AUTO)"
     if not args.no_tc:
-        tc = tc_leg(ms_tc, prof_tc, clocks_tc, "f16 in, f32 accumulate", 2.0, 1e-3)
+        tc = tc_leg(ms_tc, prof_tc, clocks_tc, "f16 in, f32 accumulate", 2.0, 1e-3, auto_unit, seq["tc"])
+        tc_mma = tc_leg(ms_tcm, prof_tcm, clocks_tcm, "f16 in, f32 accumulate", 2.0, 1e-3,
+                        "tensor cores (CORR_X_TENSOR_CORES)", seq["tc_mma"])
     if not args.no_fp8:
-        fp8 = tc_leg(ms_f8, prof_f8, clocks_f8, "e4m3 in, f32 accumulate", 1.0, 8e-2)
+        fp8 = tc_leg(ms_f8, prof_f8, clocks_f8, "e4m3 in, f32 accumulate", 1.0, 8e-2, auto_unit, seq["fp8"])
+        fp8_mma = tc_leg(ms_f8m, prof_f8m, clocks_f8m, "e4m3 in, f32 accumulate", 1.0, 8e-2,
+                         "tensor cores (CORR_X_TENSOR_CORES)", seq["fp8_mma"])
 
     # ---- end to end through the host API ----
     # The inputs live in pinned host memory and every step moves them to the
@@ -904,12 +927,14 @@ def main():
                     **sample_errors(corr, scan, hs, ref)}
         if tc is not None:
             tc["measured_rel_rms"] = measured["fp16"]
+            tc_mma["measured_rel_rms"] = measured["fp16_tensor_cores"]
         if fp8 is not None:
             fp8["measured_rel_rms"] = measured["fp8"]
+            fp8_mma["measured_rel_rms"] = measured["fp8_tensor_cores"]
         if dense is not None and dense_sample is not None:
             dsc, dprefix = dense_sample
             r2, cores2, dt2, _, dref = cpu_oracle_sample(dsc, dprefix, DENSE_SAMPLE_S, DENSE_SAMPLE_STREAMS)
-            derr = sample_errors(corr, dsc, dprefix, dref, DENSE_SAMPLE_S)
+            derr = sample_errors(corr, dsc, dprefix, dref, DENSE_SAMPLE_S, units=(0,))
             for name in ("fp32", "fp16", "fp8"):
                 dense[name]["measured_rel_rms"] = derr[name]
             dense["measured_error_sample"] = ("first %.3f s of the 64-station scan as one integration, streams 0-%d; "
@@ -940,7 +965,8 @@ def main():
                              "overlapped_stages": {k: {"ms_per_step": v[0] / args.steps,
                                                        "launches_per_step": v[1] / args.steps}
                                                    for k, v in prof_ovl.items()}},
-                "xstep_tflops": x_tflops, "tc": tc, "fp8": fp8, "e2e_copy": e2e_copy,
+                "xstep_tflops": x_tflops, "tc": tc, "tc_tensor_cores": tc_mma, "fp8": fp8,
+                "fp8_tensor_cores": fp8_mma, "e2e_copy": e2e_copy,
                 "dense": dense, "fringe": fringe, "batch": batch, "serve": served, "peaks": peaks}
         print(json.dumps(line), flush=True)
     if ws > 1:

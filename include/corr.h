@@ -107,6 +107,22 @@ int corr_set_sky_freq(corr_t *h, int subband, double nu0_hz);
  * correlate call (CORR_ESTATE). */
 int corr_set_precision(corr_t *h, int mode);
 
+/* Which unit multiplies the FP16 / FP8 spectra of the reduced-precision
+ * modes (no effect in CORR_PREC_FP32).  CORR_X_AUTO (the default): the CUDA
+ * cores for up to 12 (station, polarisation) rows of the X step (stations,
+ * or 2 x stations with both hands) and whole 128-channel tiles, where a
+ * 128-row tensor-core tile would hold at most 6 channels' worth of useful
+ * products and building its operand tiles costs more than the X step it
+ * speeds up; the tensor cores above.  CORR_X_CUDA_CORES: the CUDA cores
+ * where that form applies (else the tensor cores).  CORR_X_TENSOR_CORES:
+ * always the tensor cores.  On the CUDA cores every product of FP16 (E4M3)
+ * values is exact in FP32 and the sums are FP32, as on the tensor cores,
+ * so the result lies within the same stated bound of the FP64 definition;
+ * the order of the FP32 additions differs.  Only before the first correlate
+ * call (CORR_ESTATE); an unknown unit is CORR_EINVAL. */
+enum { CORR_X_AUTO = 0, CORR_X_CUDA_CORES = 1, CORR_X_TENSOR_CORES = 2 };
+int corr_set_x_unit(corr_t *h, int unit);
+
 /* Where the fringe rotation is applied.  CORR_ROT_POST_F (the default): after
  * the transform, one phase frac(nu0 tau(t_c)) per block and channel slope, as
  * in step 4 above.  CORR_ROT_PRE_F: before the transform, every sample x[n] of

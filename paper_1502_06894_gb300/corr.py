@@ -28,6 +28,9 @@ CORR_ETOOBIG = -8
 CORR_PREC_FP32 = 0
 CORR_PREC_FP16_TC = 1
 CORR_PREC_FP8_TC = 2
+CORR_X_AUTO = 0
+CORR_X_CUDA_CORES = 1
+CORR_X_TENSOR_CORES = 2
 CORR_ROT_POST_F = 0
 CORR_ROT_PRE_F = 1
 CORR_POL_PARALLEL = 0
@@ -66,6 +69,7 @@ _SIGS = {
     "corr_set_format": ([_H, C.c_double, _P], C.c_int),
     "corr_set_sky_freq": ([_H, C.c_int, C.c_double], C.c_int),
     "corr_set_precision": ([_H, C.c_int], C.c_int),
+    "corr_set_x_unit": ([_H, C.c_int], C.c_int),
     "corr_set_stream": ([_H, _P], C.c_int),
     "corr_set_chunk_blocks": ([_H, C.c_int], C.c_int),
     "corr_set_pipeline": ([_H, C.c_int], C.c_int),
@@ -179,6 +183,9 @@ class Correlator:
 
     def set_precision(self, mode: int):
         self._check(corr_set_precision(self.h, int(mode)))
+
+    def set_x_unit(self, unit: int):
+        self._check(corr_set_x_unit(self.h, int(unit)))
 
     def set_fringe_rotation(self, mode: int):
         self._check(corr_set_fringe_rotation(self.h, int(mode)))

@@ -128,6 +128,8 @@ struct corr_s {
   unsigned char* d_tiles[2] = {};  // tensor-core operand tiles
   bool tc_tiles = false;
   bool tc_direct = false;  // the F step writes the tiles itself
+  int x_unit = CORR_X_AUTO;  // requested unit of the X step for FP16 / FP8 spectra
+  bool x_cc = false;         // FP16 / FP8 spectra, X step on CUDA cores (FP32 products and sums)
 
   // optional per-stage CUDA-event timing of the launches
   bool profiling = false;
@@ -331,6 +333,7 @@ struct WorkLayout {
   int64_t spi = 0;
   int Mcap = 0, CB = 0, KZ = 0;
   bool tiles = false, direct = false;
+  bool cc = false;  // FP16 / FP8 spectra read by the CUDA-core X step
   int nbuf = 1;  // spectra / tile buffers: 2 when F and X overlap
   size_t spec = 0, part = 0, tiles_bytes = 0, small = 0;  // spec, tiles_bytes: per buffer
   size_t total() const { return nbuf * (spec + tiles_bytes) + part + small; }
@@ -350,8 +353,14 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   const size_t nbl = (size_t)nbl_of(S);
   w.Mcap = (int)((w.spi + h->N - 1) / h->N) + 1;
   const size_t per_block = (size_t)G * S * nch * sizeof(float2);
-  const bool tc = h->precision != CORR_PREC_FP32;
   const bool fp8 = h->precision == CORR_PREC_FP8_TC;
+  // FP16 / FP8 spectra: the X step on the tensor cores, or (up to 12
+  // (station, pol) rows, where an MMA tile would be mostly padding and the
+  // operand corner turn costs more than the X step it speeds up) on the
+  // CUDA cores from the same spectra
+  w.cc = h->precision != CORR_PREC_FP32 && h->x_unit != CORR_X_TENSOR_CORES &&
+         xstage_reduced_supported(XS, nch) && (h->x_unit == CORR_X_CUDA_CORES || XS <= 12);
+  const bool tc = h->precision != CORR_PREC_FP32 && !w.cc;
   const int kb = fp8 ? 128 : 64;  // blocks per K tile
   // the F step writes tensor-core tiles itself for FFTs of up to 2048 points
   // and post-F rotation; otherwise FP16 / FP8 spectra are corner-turned
@@ -389,7 +398,8 @@ static int work_layout(corr_t* h, WorkLayout& w) {
   // corner-turned into them
   w.tiles = tc && xtc_cpt(XS) > 0;
   w.direct = w.tiles && direct_ok;
-  w.spec = w.direct ? 16 : (w.tiles ? per_block / (fp8 ? 4 : 2) * w.CB : per_block * w.CB);
+  w.spec = w.direct ? 16
+                    : ((w.tiles || w.cc) ? per_block / (fp8 ? 4 : 2) * w.CB : per_block * w.CB);
   // partial sums: KZ slices for the FP32 X step, one for the tensor cores
   w.part = sizeof(float2) * (size_t)(tc ? 1 : w.KZ) * nbl_of(XS) * XG * nch;
   if (w.tiles) {
@@ -470,6 +480,7 @@ static int prepare(corr_t* h) {
   CK(cudaMallocHost((void**)&h->h_err, sizeof(int)), "cudaMallocHost err");
   h->tc_tiles = w.tiles;
   h->tc_direct = w.direct;
+  h->x_cc = w.cc;
   if (h->tc_tiles) {
     for (int q = 0; q < w.nbuf; ++q) {
       if ((rc = dalloc(h, (void**)&h->d_tiles[q], w.tiles_bytes, "operand tiles"))) return rc;
@@ -669,8 +680,9 @@ static FParams fparams(corr_t* h, int blk0, int cb, int slot) {
 static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, double* w_out, int slot, bool overlap) {
   const int S = h->S;
   cudaEvent_t pa = nullptr;
-  const bool tc = h->precision != CORR_PREC_FP32;
+  const bool reduced = h->precision != CORR_PREC_FP32;  // FP16 / FP8 spectra
   const bool fp8 = h->precision == CORR_PREC_FP8_TC;
+  const bool tc = h->tc_tiles;                           // X step on the tensor cores
   const int kz_used = tc ? 1 : h->KZ;
   // the X step's stations and streams (2S and nsub with both hands)
   const int XS = x_stations(h), XG = x_streams(h);
@@ -688,7 +700,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
     }
     FParams fp = fparams(h, c0, cb, slot);
     fp.out = h->d_spec[buf];
-    if (tc) {
+    if (reduced) {
       fp.out_kind = fp8 ? 2 : 1;
       fp.scale = ldexpf(1.0f, -h->sigma);
     }
@@ -745,6 +757,7 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
       }
       XParams xp;
       xp.spec = h->d_spec[buf];
+      xp.in_kind = h->x_cc ? (fp8 ? 2 : 1) : 0;
       xp.CB = cb;
       xp.S = XS;
       xp.G = XG;
@@ -783,12 +796,15 @@ static int enqueue_rest(corr_t* h, cudaStream_t st, int M, float2* vis_out, doub
   fin.err = nullptr;  // the handle reports a device timeout as CORR_ETIMEOUT
   pa = prof_begin(h, st);
   CK(launch_weights(fin, st), "weights launch");
+  // FP16 / FP8 spectra carry X 2^-sigma: the sums carry 2^(-2 sigma)
+  const float unscale = reduced ? ldexpf(1.0f, 2 * h->sigma) : 1.0f;
   if (cross_of(h)) {
     fin.G = h->nsub;
-    CK(launch_finalize_cross(fin, tc, tc ? ldexpf(1.0f, 2 * h->sigma) : 1.0f, st), "finalize launch");
+    CK(launch_finalize_cross(fin, tc, unscale, st), "finalize launch");
   } else if (tc) {
-    CK(launch_finalize_tc(fin, ldexpf(1.0f, 2 * h->sigma), st), "finalize launch");
+    CK(launch_finalize_tc(fin, unscale, st), "finalize launch");
   } else {
+    fin.unscale = unscale;
     CK(launch_finalize(fin, st), "finalize launch");
   }
   prof_end(h, 3, pa, st);
@@ -1029,6 +1045,15 @@ int corr_set_fringe_rotation(corr_t* h, int mode) {
   if (h->prepared && mode != h->rotation)
     return h->fail(CORR_ESTATE, "corr_set_fringe_rotation: only before the first correlate");
   h->rotation = mode;
+  return CORR_OK;
+}
+
+int corr_set_x_unit(corr_t* h, int unit) {
+  if (!h) return CORR_EINVAL;
+  if (unit != CORR_X_AUTO && unit != CORR_X_CUDA_CORES && unit != CORR_X_TENSOR_CORES)
+    return h->fail(CORR_EINVAL, "corr_set_x_unit: unknown unit %d", unit);
+  if (h->prepared && unit != h->x_unit) return h->fail(CORR_ESTATE, "corr_set_x_unit: only before the first correlate");
+  h->x_unit = unit;
   return CORR_OK;
 }
 

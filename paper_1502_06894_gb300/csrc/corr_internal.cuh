@@ -109,7 +109,8 @@ struct XTC2Params {
 
 // X stage: V_ab[k] += X_a[k] conj(X_b[k]) over the chunk's blocks.
 struct XParams {
-  const float2* spec;       // [G][CB][S][nchan]
+  const float2* spec;       // [G][CB][S][nchan] complex values of kind in_kind
+  int in_kind = 0;          // 0: FP32; 1: FP16 (half2); 2: E4M3 pairs (Re low byte) -- S <= 12 only
   int CB, S, G, nchan;
   int KZ;                   // block splits per chunk (one partial each)
   float2* part;             // [KZ][nbl][G][nchan]
@@ -126,6 +127,7 @@ struct FinParams {
   float2* out;              // [nbl][G][nchan]
   double* weights;          // [nbl] (device, may be null)
   const int* err;           // optional: when *err != 0 (an X-step wait timed out) the output is NaN
+  float unscale = 1.0f;     // k_finalize: times this (2^(2 sigma) after an X step on FP16 / E4M3 spectra)
 };
 
 // launchers (return cudaError_t of the launch)
@@ -148,6 +150,9 @@ int xstage_kz(int CB, int S, int G, int nchan);
 cudaError_t launch_xstage(const XParams& p, cudaStream_t s);
 cudaError_t launch_weights(const FinParams& p, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, cudaStream_t s);
+// The CUDA-core X step reads FP16 / E4M3 spectra (XParams::in_kind) for up to
+// 12 stations and whole 128-channel tiles.
+bool xstage_reduced_supported(int S, int nchan);
 int xtc_cpt(int S);
 // Spins before a device wait of the X kernels gives up (negative: the
 // default); process-wide, read at every launch.  A test hook.

@@ -51,7 +51,7 @@ __global__ void k_finalize(FinParams p) {
       v.y += x.y;
     }
     const int w = p.wcount[bl];
-    const float sc = w > 0 ? (float)(1.0 / ((double)w * (double)p.N)) : 0.f;
+    const float sc = w > 0 ? (float)((double)p.unscale / ((double)w * (double)p.N)) : 0.f;
     p.out[e] = failed ? make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000))
                       : make_float2(v.x * sc, v.y * sc);
   }

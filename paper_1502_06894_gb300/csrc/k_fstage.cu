@@ -178,6 +178,16 @@ __device__ __forceinline__ void put_chunk8(const TcTiles& o, int S, int s, int j
       make_uint2(__byte_perm(i01, i23, 0x5410), __byte_perm(i45, i67, 0x5410));
 }
 
+// Barrier of one team of 8 groups (8T threads, named barrier 1 + team) when
+// there are several teams of whole warps, else of the CTA.
+template <int T, int SPR>
+__device__ __forceinline__ void tsync(int team) {
+  if constexpr (SPR > 1 && (8 * T) % 32 == 0)
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(8 * T) : "memory");
+  else
+    __syncthreads();
+}
+
 template <int L, int GC, bool FP8>
 __global__ void __launch_bounds__(Groups<L>::T * GroupsTC<L>::NGRP, MinBlocksTC<L>::v)
 k_fstage_tc(FParams p, TcTiles o) {
@@ -185,7 +195,8 @@ k_fstage_tc(FParams p, TcTiles o) {
   constexpr int T = P::T;
   constexpr int NGRP = GroupsTC<L>::NGRP;
   static_assert(NGRP >= 8 && NGRP % 8 == 0, "the tile writer needs 8 groups per stream");
-  constexpr int SPR = NGRP / 8;  // streams per round
+  constexpr int SPR = NGRP / 8;  // teams: streams per round
+  constexpr bool TEAMS = SPR > 1 && (8 * T) % 32 == 0;
   constexpr int BUF = kBufPad<L>();
   constexpr int R0 = P::R0;
   constexpr int PER0 = L / R0 / T;
@@ -196,10 +207,10 @@ k_fstage_tc(FParams p, TcTiles o) {
   __shared__ float2 s_lut16[16];
   __shared__ float2 s_tw[Tw<L>::size];
   fill_tables<L, LastRadix<L>::v>(s_lut16, s_tw, p);
-  __syncthreads();
   const int tid = threadIdx.x;
   const int grp = tid / T;
   const int t = tid - grp * T;
+  const int team = grp / 8;
   float2* fbuf = fbuf_all + grp * BUF;
   const int s = blockIdx.y;
   const int G = GC ? GC : p.G;
@@ -215,12 +226,16 @@ k_fstage_tc(FParams p, TcTiles o) {
   const int kt = (blockIdx.x * 8) / KB;
   const int kc = FP8 ? ((blockIdx.x & 15) >> 1) : (blockIdx.x & 7);  // 16-byte chunk of the K range
   const int khalf = FP8 ? (blockIdx.x & 1) * 8 : 0;   // byte offset of the FP8 half chunk
+  __syncthreads();
 
   for (int r0 = 0; r0 < G; r0 += SPR) {
-    const int j = r0 + grp / 8;
+    const int j = r0 + team;
     const bool ok = valid && j < G;
-    // ---- pass 0 from global memory (skipped for blocks that are absent or
-    //      not valid: their spectra are zeros) ----
+    // the stream's fringe phase, loaded now so that its latency passes during the transform
+    const float phi = ok ? p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d] : 0.f;
+    // ---- pass 0 from global memory (L1-cached across the stream rounds),
+    //      skipped for blocks that are absent or not valid: their spectra
+    //      are zeros ----
     if (ok) {
       float2 v[PER0][R0];
 #pragma unroll
@@ -253,7 +268,6 @@ k_fstage_tc(FParams p, TcTiles o) {
     //      barrier and holds nothing in registers ----
     constexpr int QF = HALF / T;  // k = t + qT < HALF for q < QF; k = HALF is thread 0's extra
     if (ok) {
-      const float phi = p.phi[((size_t)s * p.nsub + j / p.npol) * p.ld + d];
       float2 z = cis_turns(fmaf((float)t, delta, phi));
       float2 y = cis_turns(fmaf((float)(L - t), delta, phi));
       float cm1, sn;
@@ -280,13 +294,18 @@ k_fstage_tc(FParams p, TcTiles o) {
       for (int q = 0; q < QF; ++q) put_pair<FP8>(fbuf + padp<R0>(t + q * T), zero, zero, o.scale);
       if (t == 0) put_pair<FP8>(fbuf + padp<R0>(HALF), zero, zero, o.scale);
     }
-    __syncthreads();
+    tsync<T, SPR>(team);
 
     // ---- corner turn: for each channel pair (c, L - c) the 8 blocks' slots
-    //      become, per channel and Re/Im, one 16-byte chunk (FP8: 8 bytes) ----
-    for (int it = tid; it < SPR * (HALF + 1); it += NGRP * T) {
-      const int ss = it / (HALF + 1);
-      const int c = it - ss * (HALF + 1);
+    //      become, per channel and Re/Im, one 16-byte chunk (FP8: 8 bytes);
+    //      with teams each team turns its own stream ----
+    const int ss0 = TEAMS ? team : 0;
+    const int nss = TEAMS ? 1 : SPR;
+    const int ttid = TEAMS ? tid - team * 8 * T : tid;
+    const int tstride = TEAMS ? 8 * T : NGRP * T;
+    for (int it = ttid; it < nss * (HALF + 1); it += tstride) {
+      const int ss = ss0 + it / (HALF + 1);
+      const int c = it - (ss - ss0) * (HALF + 1);
       const int jo = r0 + ss;
       if (jo >= G) continue;
       const float2* slot0 = fbuf_all + (size_t)(ss * 8) * BUF + padp<R0>(c);
@@ -304,7 +323,7 @@ k_fstage_tc(FParams p, TcTiles o) {
         if (c != 0 && c != HALF) put_chunk16(o, p.S, s, jo, kt, kc, L - c, w, 1);
       }
     }
-    __syncthreads();
+    tsync<T, SPR>(team);
   }
 }
 

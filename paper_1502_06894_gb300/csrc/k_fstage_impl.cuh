@@ -119,20 +119,45 @@ __device__ __forceinline__ void gsync(int grp) {
   }
 }
 
-// v[r] *= W^{kr} for r = 1..R-1 from wp[i] = W^{k 2^i}: W^{kr} is wp of r's
-// highest bit times W^{k(r - that bit)} (indices fixed at compile time, so
-// every value stays in registers).
-template <int R, int LOGR, int r = 1>
-__device__ __forceinline__ void twiddle_products(float2 (&v)[R], float2 (&w)[R], const float2 (&wp)[LOGR]) {
-  if constexpr (r < R) {
+// v[r] *= W^{kr} for r = 1..R-1 from wp[i] = W^{k 2^i}.  r splits into its
+// low LO bits a and its high bits b: W^{kr} = A[a] B[b] with A[a] = W^{ka}
+// and B[b] = W^{k 2^LO b}, each the product of the wp of its bits.  Only the
+// two short tables stay live (not one power per r), and every index is fixed
+// at compile time, so all values stay in registers.
+template <int N, int r = 1>
+__device__ __forceinline__ void power_table(float2 (&A)[N], const float2* wp) {
+  if constexpr (r < N) {
     constexpr int hb = ilog2c(r);
     if constexpr (r == (1 << hb))
-      w[r] = wp[hb];
+      A[r] = wp[hb];
     else
-      w[r] = cmul(w[r - (1 << hb)], wp[hb]);
-    v[r] = cmul(v[r], w[r]);
-    twiddle_products<R, LOGR, r + 1>(v, w, wp);
+      A[r] = cmul(A[r - (1 << hb)], wp[hb]);
+    power_table<N, r + 1>(A, wp);
   }
+}
+
+template <int R, int NA, int NB, int r = 1>
+__device__ __forceinline__ void apply_powers(float2 (&v)[R], const float2 (&A)[NA], const float2 (&B)[NB]) {
+  if constexpr (r < R) {
+    constexpr int a = r % NA, b = r / NA;
+    if constexpr (a != 0 && b != 0)
+      v[r] = cmul(cmul(v[r], A[a]), B[b]);
+    else if constexpr (a != 0)
+      v[r] = cmul(v[r], A[a]);
+    else
+      v[r] = cmul(v[r], B[b]);
+    apply_powers<R, NA, NB, r + 1>(v, A, B);
+  }
+}
+
+template <int R, int LOGR>
+__device__ __forceinline__ void twiddle_products(float2 (&v)[R], const float2 (&wp)[LOGR]) {
+  constexpr int LO = LOGR / 2;
+  constexpr int NA = 1 << LO, NB = 1 << (LOGR - LO);
+  float2 A[NA], B[NB];
+  power_table<NA>(A, wp);
+  power_table<NB>(B, wp + LO);
+  apply_powers<R, NA, NB>(v, A, B);
 }
 
 // A later Stockham pass: read R points per butterfly group, twiddle, DFT,
@@ -146,18 +171,22 @@ __device__ __forceinline__ void twiddle_products(float2 (&v)[R], float2 (&w)[R],
 // which keeps the memory pipeline, the bottleneck of the large transforms,
 // to log2 R loads per butterfly group.  Those loads depend on the thread
 // only, so they are issued first and their latency passes while the group
-// reads its points and waits at the barrier.
+// reads its points and waits at the barrier.  With s_twp (transforms of
+// 2048+ points) the powers come from a shared table [i][k] of the pass
+// instead: consecutive k in consecutive words, read after the barrier.
 template <int L, int R, int NS, int T, int P, int TWS = 2>
 __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, int grp,
                                               const float2* __restrict__ twN,
-                                              const float2* __restrict__ s_twl = nullptr) {
+                                              const float2* __restrict__ s_twl = nullptr,
+                                              const float2* __restrict__ s_twp = nullptr) {
   constexpr int GROUPS = L / R;
   constexpr int PER = GROUPS / T;
   constexpr int LOGR = ilog2c(R);
   static_assert(PER >= 1 && GROUPS % T == 0, "bad FFT plan");
   const bool tab = NS * R == L && s_twl != nullptr;
+  const bool ptab = !tab && s_twp != nullptr;  // the powers from the shared table of this pass
   float2 wp[PER][LOGR];
-  if (!tab) {
+  if (!tab && !ptab) {
 #pragma unroll
     for (int u = 0; u < PER; ++u) {
       const int k = (t + u * T) & (NS - 1);
@@ -181,8 +210,11 @@ __device__ __forceinline__ void stockham_pass(float2* __restrict__ buf, int t, i
 #pragma unroll
       for (int r = 1; r < R; ++r) v[u][r] = cmul(v[u][r], s_twl[r * NS + k]);
     } else {
-      float2 w[R];
-      twiddle_products<R, LOGR>(v[u], w, wp[u]);
+      if (ptab) {
+#pragma unroll
+        for (int i = 0; i < LOGR; ++i) wp[u][i] = s_twp[i * NS + k];
+      }
+      twiddle_products<R, LOGR>(v[u], wp[u]);
     }
     dft_reg<R>(v[u]);
     const int idxD = (j / NS) * NS * R + k;
@@ -214,11 +246,11 @@ template <int L> struct Groups {
   // 256-thread transforms per CTA of 1024 threads, so that barriers stay
   // within a transform, four of them are in flight per SM and 32 warps hide
   // the latency of the twiddle loads
-  static constexpr int NGRP = T == 1 ? 64 : (L == 4096 ? 4 : 256 / T);
+  static constexpr int NGRP = T == 1 ? 64 : (L == 4096 ? 3 : 256 / T);
 };
 
-// The tensor-core F step runs 8 groups per stream round (one per block of
-// its 8), or a multiple of 8 when the groups are small.
+// The tensor-core F step runs teams of 8 groups (one per block of its 8),
+// one stream per team and round.
 template <int L> struct GroupsTC {
   static constexpr int NGRP = Groups<L>::NGRP >= 8 ? Groups<L>::NGRP : 8;
 };
@@ -249,6 +281,34 @@ __device__ __forceinline__ void fill_tables(float2* s_lut16, float2* s_tw, const
       s_tw[e] = __ldg(&p.twN[TWS * k * r]);
     }
     for (int k = tid; k <= L / 2; k += blockDim.x) s_tw[L + k] = __ldg(&p.twN[k]);
+  }
+}
+
+// Shared tables of the powers W^{k 2^i} (k < NS, i < log2 R) of the passes
+// after the first, for transforms of 2048+ points: [i][k] per pass, the
+// second pass's table after the first's.
+template <int L> struct PassTw {
+  static constexpr bool on = L >= 2048;
+  static constexpr int n1 = Plan<L>::R1 > 1 ? ilog2c(Plan<L>::R1) * Plan<L>::R0 : 0;
+  static constexpr int n2 = Plan<L>::R2 > 1 ? ilog2c(Plan<L>::R2) * Plan<L>::R0 * Plan<L>::R1 : 0;
+  static constexpr int size = on ? n1 + n2 : 1;
+};
+
+template <int L, int R, int NS, int TWS>
+__device__ __forceinline__ void fill_pass_table(float2* dst, const float2* __restrict__ twN) {
+  constexpr int LOGR = ilog2c(R);
+  for (int e = threadIdx.x; e < LOGR * NS; e += blockDim.x) {
+    const int i = e / NS, k = e - i * NS;
+    dst[e] = __ldg(&twN[TWS * k * (1 << i) * (L / (NS * R))]);
+  }
+}
+
+template <int L, int TWS>
+__device__ __forceinline__ void fill_pass_tables(float2* s_twp, const float2* __restrict__ twN) {
+  if constexpr (PassTw<L>::on) {
+    using P = Plan<L>;
+    if constexpr (P::R1 > 1) fill_pass_table<L, P::R1, P::R0, TWS>(s_twp, twN);
+    if constexpr (P::R2 > 1) fill_pass_table<L, P::R2, P::R0 * P::R1, TWS>(s_twp + PassTw<L>::n1, twN);
   }
 }
 
@@ -644,7 +704,9 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
   __shared__ int s_ok[2][64];
   __shared__ float2 s_lut16[16];
   __shared__ float2 s_tw[Tw<L>::size];
+  __shared__ float2 s_twp[PassTw<L>::size];
   fill_tables<L, LastRadix<L>::v, TWS>(s_lut16, s_tw, p);
+  fill_pass_tables<L, TWS>(s_twp, p.twN);
 
   stage_windows<N, GC>(p, sv, s, G, first, min(slots, p.CB - first), wbuf, wslot, s_ok[0], s_boff[0]);
   cp_async_commit();
@@ -720,8 +782,11 @@ k_fstage(FParams p, int slots, int wslot, int nseq) {
         }
         gsync<T>(grp);
         if constexpr (P::R1 > 1)
-          stockham_pass<L, P::R1, P::R0, T, P::R0, TWS>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr);
-        if constexpr (P::R2 > 1) stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0, TWS>(fbuf, t, grp, p.twN);
+          stockham_pass<L, P::R1, P::R0, T, P::R0, TWS>(fbuf, t, grp, p.twN, Tw<L>::on ? s_tw : nullptr,
+                                                        PassTw<L>::on ? s_twp : nullptr);
+        if constexpr (P::R2 > 1)
+          stockham_pass<L, P::R2, P::R0 * P::R1, T, P::R0, TWS>(fbuf, t, grp, p.twN, nullptr,
+                                                                PassTw<L>::on ? s_twp + PassTw<L>::n1 : nullptr);
       }
 
       // ---- store (real split and post-F rotation, or the pre-F path's slope) ----
@@ -774,10 +839,10 @@ static cudaError_t launch_LG(const FParams& p, cudaStream_t st) {
   }
   const int64_t steps = (int64_t)((p.CB + slots - 1) / slots) * p.S;
   int nseq = 1;
-  if ((size_t)MinBlocks<L>::v * (two + sizeof(float2) * Tw<L>::size + 1024) <= 227 * 1024)
+  if ((size_t)MinBlocks<L>::v * (two + sizeof(float2) * (Tw<L>::size + PassTw<L>::size) + 1024) <= 227 * 1024)
     nseq = (int)std::max<int64_t>(1, std::min<int64_t>(4, steps / ((int64_t)8 * MinBlocks<L>::v * sm_count)));
   const size_t smem = nseq > 1 ? two : one;
-  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (smem + sizeof(float2) * (Tw<L>::size + PassTw<L>::size) + 1024 > 227 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(k_fstage<L, GC, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int per_cta = slots * nseq;

@@ -381,22 +381,24 @@ constexpr int kTurnRow = 144;  // bytes per staged row (128 bytes of values + 16
 // one whole 128-byte line.
 __device__ __forceinline__ void write_staged_rows(const unsigned char* turn_raw, const TcTiles& o, int S, int nch,
                                                   int CH, int c0, int kt, int jo) {
-  const int nitems = 2 * S * nch * 8;
-  for (int i = threadIdx.x; i < nitems; i += blockDim.x) {
-    const int kc = i & 7;
-    const int row = i >> 3;  // (ri * S + s) * nch + c
-    const int c = row % nch;
-    const int rs = row / nch;
-    const int s = rs % S;
-    const int ri = rs / S;
+  // a thread keeps one (channel, 16-byte chunk) pair and runs over the 2S
+  // rows (station, Re/Im) of that channel: the tile coordinates of the
+  // channel are divided out once per thread, not once per chunk
+  const int per = CH * 8;                  // (channel, chunk) pairs; CH * 8 divides the 256 threads
+  const int comb = threadIdx.x & (per - 1);
+  const int c = comb >> 3, kc = comb & 7;
+  if (c >= nch) return;
+  const int k = c0 + c;
+  const int sl = k / o.W;
+  const int cw = k - sl * o.W;
+  const int tg = cw / o.cpt;
+  const int cl = cw - tg * o.cpt;
+  unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
+  for (int rs = threadIdx.x / per; rs < 2 * S; rs += blockDim.x / per) {
+    const int ri = rs >= S ? 1 : 0;
+    const int s = rs - ri * S;
     const uint4 v = *reinterpret_cast<const uint4*>(turn_raw + ((size_t)rs * CH + c) * kTurnRow + kc * 16);
-    const int k = c0 + c;
-    const int sl = k / o.W;
-    const int cw = k - sl * o.W;
-    const int tg = cw / o.cpt;
-    const int cl = cw - tg * o.cpt;
     const int r = (cl * S + s) * 2 + ri;
-    unsigned char* tile = o.tiles + ((((size_t)jo * o.nslice + sl) * o.NKT + kt) * 2 + tg) * 16384;
     *reinterpret_cast<uint4*>(tile + (r >> 3) * 1024 + (r & 7) * 128 + ((kc ^ (r & 7)) << 4)) = v;
   }
 }
@@ -414,13 +416,16 @@ __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec,
   // 4 Im values as one 8-byte piece of each row.  Threads run over blocks
   // fastest, so a half-warp fills 64-byte runs of two rows that sit in
   // different banks (rows 4 apart are 576 bytes apart).
-  const int CV = CH / 4;
-  const int nstage = S * 2 * CV * 8;
+  const int lcv = CH == 16 ? 2 : (CH == 8 ? 1 : 0);  // CV = CH / 4 = 2^lcv
+  const int nstage = S * 2 * (8 << lcv);
+  // two iterations' loads in flight per thread (the kernel is bound by the
+  // latency of its HBM reads)
+#pragma unroll 2
   for (int i = tid; i < nstage; i += blockDim.x) {
     const int b4 = i & 7;
     const int j = i >> 3;
-    const int c = 4 * (j % CV);
-    const int rest = j / CV;
+    const int c = 4 * (j & ((1 << lcv) - 1));
+    const int rest = j >> lcv;
     const int bh = rest & 1;
     const int sb = rest >> 1;
     const int b0 = bh * 32 + b4 * 4;
@@ -460,13 +465,14 @@ __global__ void __launch_bounds__(256) k_tiles8(const uint16_t* __restrict__ spe
   const int jo = blockIdx.z;
   const int nch = min(CH, nchan - c0);
   const int tid = threadIdx.x;
-  const int CV = CH / 8;
-  const int nstage = S * CV * 32;
+  const int lcv = CH == 16 ? 1 : 0;  // CV = CH / 8 = 2^lcv
+  const int nstage = S * (32 << lcv);
+#pragma unroll 2
   for (int i = tid; i < nstage; i += blockDim.x) {
     const int b4 = i & 31;
     const int j = i >> 5;
-    const int c = 8 * (j % CV);
-    const int sb = j / CV;
+    const int c = 8 * (j & ((1 << lcv) - 1));
+    const int sb = j >> lcv;
     uint4 v[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {

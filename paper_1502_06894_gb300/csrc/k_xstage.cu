@@ -13,6 +13,8 @@
 #include "corr_internal.cuh"
 
 #include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <type_traits>
 #include <cudaTypedefs.h>
 
@@ -216,11 +218,36 @@ __device__ __forceinline__ uint32_t xs_u32(const void* ptr) { return (uint32_t)_
 // so twice the warps share one ring of spectra.
 constexpr int kXThreadsT = 2 * kXT;
 
-template <int TA>
+// Bytes per spectrum value of each input kind: FP32 complex, FP16 complex
+// (half2), E4M3 complex (two bytes, Re low).
+// Blocks per ring stage: 2 of FP32, 4 of FP16, 8 of E4M3 values, so that a
+// stage (and the bytes in flight per CTA) is the same size for every kind.
+template <int IN> struct SpecElem {
+  static constexpr int bytes = IN == 0 ? 8 : (IN == 1 ? 4 : 2);
+  static constexpr int nb = kNB * 8 / bytes;
+};
+
+// One spectrum value from the ring as FP32 (the FP16 / E4M3 values carry
+// X * 2^-sigma; the normalisation takes the 2^(2 sigma) back out).
+template <int IN>
+__device__ __forceinline__ float2 ring_value(const unsigned char* st, int idx) {
+  if constexpr (IN == 0) {
+    return reinterpret_cast<const float2*>(st)[idx];
+  } else if constexpr (IN == 1) {
+    return __half22float2(reinterpret_cast<const __half2*>(st)[idx]);
+  } else {
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2(reinterpret_cast<const __nv_fp8x2_storage_t*>(st)[idx], __NV_E4M3);
+    return __half22float2(__half2(h));
+  }
+}
+
+template <int TA, int IN>
 __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__ CUtensorMap tmap, XParams p) {
   extern __shared__ __align__(1024) unsigned char xs_tma_raw[];
   const uint32_t raw = xs_u32(xs_tma_raw);
-  float2* ring = reinterpret_cast<float2*>(xs_tma_raw + (((raw + 1023u) & ~1023u) - raw));  // [kStagesX][kNB*S][kXT]
+  constexpr int EB = SpecElem<IN>::bytes;
+  constexpr int NB = SpecElem<IN>::nb;
+  unsigned char* ring = xs_tma_raw + (((raw + 1023u) & ~1023u) - raw);  // [kStagesX][NB*S][kXT] values
   __shared__ __align__(8) uint64_t full[kStagesX];
   __shared__ int s_abort;
   const int tid = threadIdx.x;
@@ -234,9 +261,9 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
   const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
   const int b_hi = (int)((int64_t)p.CB * (kz + 1) / p.KZ);
   if (b_hi <= b_lo) return;
-  const int nst = (b_hi - b_lo + kNB - 1) / kNB;
-  const int stage_elems = kNB * S * kXT;
-  const uint32_t stage_bytes = (uint32_t)stage_elems * 8u;
+  const int nst = (b_hi - b_lo + NB - 1) / NB;
+  const int stage_elems = NB * S * kXT;
+  const uint32_t stage_bytes = (uint32_t)stage_elems * EB;
   if (tid == 0) {
     for (int i = 0; i < kStagesX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(xs_u32(&full[i])));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -247,13 +274,13 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
   auto issue = [&](int q) {
     if (q >= nst) return;
     const int slot = q % kStagesX;
-    const int row = (g * p.CB + b_lo + q * kNB) * S;
+    const int row = (g * p.CB + b_lo + q * NB) * S;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(xs_u32(&full[slot])),
                  "r"(stage_bytes)
                  : "memory");
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            xs_u32(ring + slot * stage_elems)),
+            xs_u32(ring + (size_t)slot * stage_bytes)),
         "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(2 * k0), "r"(row), "r"(xs_u32(&full[slot]))
         : "memory");
   };
@@ -286,13 +313,13 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
       if (!ok) s_abort = 1;
       __syncthreads();
       if (s_abort) break;
-      const float2* st = ring + slot * stage_elems;
+      const unsigned char* st = ring + (size_t)slot * stage_bytes;
 #pragma unroll
-      for (int bi = 0; bi < kNB; ++bi) {
-        if (b_lo + q * kNB + bi >= b_hi) break;
+      for (int bi = 0; bi < NB; ++bi) {
+        if (b_lo + q * NB + bi >= b_hi) break;
         float2 a[TA];
 #pragma unroll
-        for (int i = I0; i < TA; ++i) a[i] = i < S ? st[(bi * S + i) * kXT + lane_ch] : make_float2(0.f, 0.f);
+        for (int i = I0; i < TA; ++i) a[i] = i < S ? ring_value<IN>(st, (bi * S + i) * kXT + lane_ch) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int i = I0; i < I1; ++i) {
           const float2 ar = rot_conj(a[i]);
@@ -357,29 +384,44 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-template <int TA>
-static cudaError_t launch_tma(const XParams& p_in, cudaStream_t s, bool* used) {
+// The tensor map views the spectra as rows (stream, block, station) of 2 nchan
+// scalars (Re, Im interleaved): FP32, FP16 or single bytes (E4M3 pairs); a
+// stage is 2 x 128 scalars (128 channels, 256..1024 bytes, a multiple of 16)
+// by NB * S rows (NB blocks per stage), from x = 2 k0 (a multiple of 256 scalars).
+template <int TA, int IN>
+static cudaError_t launch_tma_in(const XParams& p_in, cudaStream_t s, bool* used) {
   *used = false;
   XParams p = p_in;
   p.wait_limit = wait_limit();
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc || p.nchan < kXT || kNB * p.S > 256) return cudaSuccess;
+  constexpr int EB = SpecElem<IN>::bytes;
+  constexpr int NB = SpecElem<IN>::nb;
+  if (!enc || p.nchan < kXT || p.nchan % kXT || NB * p.S > 256) return cudaSuccess;
   CUtensorMap tm;
   cuuint64_t dims[2] = {(cuuint64_t)2 * p.nchan, (cuuint64_t)p.G * p.CB * p.S};
-  cuuint64_t strides[1] = {(cuuint64_t)2 * p.nchan * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)(2 * kXT), (cuuint32_t)(kNB * p.S)};
+  cuuint64_t strides[1] = {(cuuint64_t)p.nchan * EB};
+  cuuint32_t box[2] = {(cuuint32_t)(2 * kXT), (cuuint32_t)(NB * p.S)};
   cuuint32_t estr[2] = {1, 1};
-  if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(p.spec), dims, strides, box, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+  const CUtensorMapDataType dt =
+      IN == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : (IN == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+  if (enc(&tm, dt, 2, const_cast<float2*>(p.spec), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return cudaSuccess;  // fall back to the cp.async ring
-  const size_t smem = 1024 + (size_t)kStagesX * kNB * p.S * kXT * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_xmac_tma<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;  // FP32: fall back to the cp.async ring
+  const size_t smem = 1024 + (size_t)kStagesX * NB * p.S * kXT * EB;
+  cudaError_t e = cudaFuncSetAttribute(k_xmac_tma<TA, IN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((p.nchan + kXT - 1) / kXT, p.G, p.KZ);
-  k_xmac_tma<TA><<<grid, kXThreadsT, smem, s>>>(tm, p);
+  k_xmac_tma<TA, IN><<<grid, kXThreadsT, smem, s>>>(tm, p);
   *used = true;
   return cudaGetLastError();
+}
+
+template <int TA>
+static cudaError_t launch_tma(const XParams& p, cudaStream_t s, bool* used) {
+  if (p.in_kind == 1) return launch_tma_in<TA, 1>(p, s, used);
+  if (p.in_kind == 2) return launch_tma_in<TA, 2>(p, s, used);
+  return launch_tma_in<TA, 0>(p, s, used);
 }
 
 static int tile_for(int S) {
@@ -410,6 +452,7 @@ static cudaError_t launch_ring(const XParams& p, cudaStream_t s) {
   bool used = false;
   cudaError_t te = launch_tma<TA>(p, s, &used);
   if (te != cudaSuccess || used) return te;
+  if (p.in_kind != 0) return cudaErrorNotSupported;  // FP16 / E4M3 spectra: the TMA ring only
   const size_t smem = (size_t)kStagesX * kNB * p.S * kXT * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_xmac_ring<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -433,8 +476,14 @@ static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
+bool xstage_reduced_supported(int S, int nchan) {
+  return S >= 1 && S <= 12 && SpecElem<2>::nb * S <= 256 && nchan >= kXT && nchan % kXT == 0 &&
+         tensor_map_encoder() != nullptr;
+}
+
 cudaError_t launch_xstage(const XParams& p, cudaStream_t s) {
   if (p.CB <= 0) return cudaSuccess;
+  if (p.in_kind != 0 && !xstage_reduced_supported(p.S, p.nchan)) return cudaErrorNotSupported;
   switch (tile_for(p.S)) {
     case 2: return launch_ring<2>(p, s);
     case 4: return launch_ring<4>(p, s);

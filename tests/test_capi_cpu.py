@@ -83,3 +83,4 @@ def test_fringe_search_checks_arguments_before_any_device_work(lib):
     assert L.corr_fringe_search(dummy, 0, 8, 4, 8, dummy, None, None, None, None, None) == -1
     for nr, nd in ((3, 8), (4, 12), (2, 8), (4, 4), (32768, 8), (8192, 16384)):
         assert L.corr_fringe_search(dummy, 4, 8, nr, nd, dummy, None, None, None, None, None) == -1, (nr, nd)
+

@@ -48,9 +48,11 @@ def rel_rms_per_baseline(v, ref):
     return np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=1) / np.sum(np.abs(ref) ** 2, axis=1))
 
 
-def run_tc(corr, sc, streams, nint, precision=None):
+def run_tc(corr, sc, streams, nint, precision=None, unit=None):
     c = corr.from_scan(sc, streams)
     c.set_precision(corr.CORR_PREC_FP16_TC if precision is None else precision)
+    if unit is not None:
+        c.set_x_unit(unit)
     outs, ws = [], []
     for _ in range(nint):
         r = c.correlate()
@@ -77,19 +79,30 @@ def check(sc, vis, w, ref, wref, nint, label, tol=TOL_FP16, name="FP16"):
         worst = max(worst, float(err.max()))
         eff = min(eff, efficiency(v, ref[i]))
         assert np.all(err < tol), (label, i, err.max())
-    print("%s: %s tensor-core X step, max rel-RMS per baseline %.3e, efficiency %.6f" % (label, name, worst, eff))
+    print("%s: %s X step, max rel-RMS per baseline %.3e, efficiency %.6f" % (label, name, worst, eff))
     return worst
 
 
-def test_tc_config2_slice(corr):
-    """10 stations, 8 subbands x 2 pols, 1024 channels: 6 channels of 20
-    rows per 128-row tile, 12-channel work items, a 0.05 s integration of
-    781.25 blocks (ragged last K tile)."""
+UNITS = pytest.mark.parametrize("unit", ["tensor", "auto"])
+
+
+def unit_of(corr, name):
+    return corr.CORR_X_TENSOR_CORES if name == "tensor" else corr.CORR_X_AUTO
+
+
+def test_tc_config2_slice(corr, unit):
+    """10 stations, 8 subbands x 2 pols, 1024 channels: on the tensor cores
+    6 channels of 20 rows per 128-row tile, 12-channel work items, a 0.05 s
+    integration of 781.25 blocks (ragged last K tile); by default (10
+    stations) the FP16 spectra go to the CUDA-core X step."""
     sc = synth.config2(seed=2, duration=0.1, tint=0.05, boundary=0.05)
     streams = [synth.station_bytes(sc, s, physics=False) for s in range(sc.stations)]
     ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
-    vis, w = run_tc(corr, sc, streams, 2)
-    check(sc, vis, w, ref, wref, 2, "cfg2 slice")
+    vis, w = run_tc(corr, sc, streams, 2, unit=unit_of(corr, unit))
+    check(sc, vis, w, ref, wref, 2, "cfg2 slice (%s)" % unit)
+
+
+test_tc_config2_slice = UNITS(test_tc_config2_slice)
 
 
 def test_tc_64_stations(corr):
@@ -107,13 +120,16 @@ def test_tc_64_stations(corr):
     check(sc, vis, w, ref, wref, 2, "64 stations")
 
 
+@UNITS
 @pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (128, 33, 1, 1),
                                                (2048, 5, 3, 1), (32, 64, 1, 1)])
-def test_tc_shapes(corr, nchan, S, nsub, npol):
+def test_tc_shapes(corr, nchan, S, nsub, npol, unit):
     """Tiles of 32, 21, 9 and 1 channels, odd stream counts, a slice wider
     than the band, 8-byte copies; 4096-point FFTs whose FP16 spectra are
     corner-turned into tiles (12 channels per tile pair, a ragged last
-    corner-turn CTA); 64 stations, one channel per tile."""
+    corner-turn CTA); 64 stations, one channel per tile.  By default the
+    shapes of up to 12 stations and 128+ channels take the CUDA-core X step
+    on the same FP16 spectra."""
     fs = 32e6
     N = 2 * nchan
     tint = round((300 * N + 5) / fs * fs) / fs
@@ -121,8 +137,8 @@ def test_tc_shapes(corr, nchan, S, nsub, npol):
                        nsub=nsub, npol=npol)
     streams = [synth.station_bytes(sc, s, physics=False) for s in range(S)]
     ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
-    vis, w = run_tc(corr, sc, streams, 2)
-    check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d" % (S, nchan, nsub * npol))
+    vis, w = run_tc(corr, sc, streams, 2, unit=unit_of(corr, unit))
+    check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d (%s)" % (S, nchan, nsub * npol, unit))
 
 
 def test_tc_rejects_more_than_64_stations(corr):
@@ -151,14 +167,16 @@ def test_tc_two_bit_efficiency_config1(corr, cfg1):
 
 # ---- FP8 (E4M3) spectra -----------------------------------------------------
 
-def test_fp8_config2_slice(corr):
+@UNITS
+def test_fp8_config2_slice(corr, unit):
     """FP8 tiles written by the F step itself (1024 channels, 128-block K
-    tiles, a ragged last tile of the 781.25-block integration)."""
+    tiles, a ragged last tile of the 781.25-block integration), or by
+    default E4M3 spectra read by the CUDA-core X step."""
     sc = synth.config2(seed=2, duration=0.1, tint=0.05, boundary=0.05)
     streams = [synth.station_bytes(sc, s, physics=False) for s in range(sc.stations)]
     ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
-    vis, w = run_tc(corr, sc, streams, 2, corr.CORR_PREC_FP8_TC)
-    check(sc, vis, w, ref, wref, 2, "cfg2 slice", TOL_FP8, "FP8")
+    vis, w = run_tc(corr, sc, streams, 2, corr.CORR_PREC_FP8_TC, unit=unit_of(corr, unit))
+    check(sc, vis, w, ref, wref, 2, "cfg2 slice (%s)" % unit, TOL_FP8, "FP8")
 
 
 def test_fp8_64_stations(corr):
@@ -175,9 +193,10 @@ def test_fp8_64_stations(corr):
     check(sc, vis, w, ref, wref, 2, "64 stations", TOL_FP8, "FP8")
 
 
+@UNITS
 @pytest.mark.parametrize("nchan,S,nsub,npol", [(256, 2, 1, 1), (64, 3, 3, 1), (512, 7, 2, 2), (2048, 5, 3, 1),
                                                (32, 64, 1, 1)])
-def test_fp8_shapes(corr, nchan, S, nsub, npol):
+def test_fp8_shapes(corr, nchan, S, nsub, npol, unit):
     """Direct FP8 tiles at several tile fillings and stream counts, and the
     FP8 corner turn for 4096-point FFTs; about 300 blocks per integration,
     so each integration ends in a ragged 128-block K tile."""
@@ -188,8 +207,8 @@ def test_fp8_shapes(corr, nchan, S, nsub, npol):
                        nsub=nsub, npol=npol)
     streams = [synth.station_bytes(sc, s, physics=False) for s in range(S)]
     ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
-    vis, w = run_tc(corr, sc, streams, 2, corr.CORR_PREC_FP8_TC)
-    check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d" % (S, nchan, nsub * npol), TOL_FP8, "FP8")
+    vis, w = run_tc(corr, sc, streams, 2, corr.CORR_PREC_FP8_TC, unit=unit_of(corr, unit))
+    check(sc, vis, w, ref, wref, 2, "S=%d nchan=%d G=%d (%s)" % (S, nchan, nsub * npol, unit), TOL_FP8, "FP8")
 
 
 def test_fp8_two_bit_efficiency_config1(corr, cfg1):
@@ -214,4 +233,30 @@ def test_fp8_rejects_more_than_64_stations(corr):
     with pytest.raises(corr.CorrError) as ei:
         c.set_precision(corr.CORR_PREC_FP8_TC)
     assert ei.value.code == corr.CORR_EINVAL
+    c.close()
+
+
+def test_cuda_core_and_tensor_core_x_agree(corr):
+    """The two units multiply the same FP16 spectra (the F kernels share
+    their arithmetic): exact products, FP32 sums in another order (and the
+    tensor cores' own accumulation), so the results agree far inside the
+    FP16 bound (5e-5 against 1e-3), and the weights are identical."""
+    sc = synth.config2(seed=21, duration=0.02, tint=0.01, boundary=0.01, nchan=512, stations=6, nsub=2, npol=1)
+    streams = [synth.station_bytes(sc, s, physics=False) for s in range(sc.stations)]
+    vt, wt = run_tc(corr, sc, streams, 2, unit=corr.CORR_X_TENSOR_CORES)
+    vc, wc = run_tc(corr, sc, streams, 2, unit=corr.CORR_X_CUDA_CORES)
+    assert np.array_equal(wt, wc)
+    for i in range(2):
+        err = rel_rms_per_baseline(vc[i].reshape(sc.nbl, -1), vt[i].reshape(sc.nbl, -1))
+        assert np.all(err < 5e-5), err.max()
+
+
+def test_x_unit_argument_errors(corr):
+    c = corr.Correlator(4, 1, 1, 256, 0.001)
+    for unit in (corr.CORR_X_AUTO, corr.CORR_X_CUDA_CORES, corr.CORR_X_TENSOR_CORES):
+        c.set_x_unit(unit)
+    for bad in (-1, 3):
+        with pytest.raises(corr.CorrError) as ei:
+            c.set_x_unit(bad)
+        assert ei.value.code == corr.CORR_EINVAL
     c.close()
