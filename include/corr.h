@@ -388,9 +388,11 @@ int corr_fringe_search(const float *dev_vis, int nsub, int nchan, int pad_rate, 
  * 8*nbl*subbands*pols*nchan bytes) is rejected with CORR_ETOOBIG.
  *
  * The first call on a device resolves the array's device address and loads
- * the FFT constants for that device (no allocation); make that first call
- * before any stream capture.  (After a cudaDeviceReset the next call does
- * this set-up again for the device's new context.)  Each call copies the
+ * the FFT constants for that device (no allocation).  (After a
+ * cudaDeviceReset the next call does this set-up again for the device's new
+ * context.)  The calls are not meant for stream capture into a CUDA graph:
+ * their copies of the caller's host descriptor arrays would be replayed from
+ * the capturing call's host pointers.  Each call copies the
  * caller's descriptor arrays below from host memory with cudaMemcpyAsync on
  * cuda_stream, writes the station views and FFT twiddles it derives itself
  * with small kernels (their values travel as kernel parameters), and only
