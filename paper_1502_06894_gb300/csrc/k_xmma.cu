@@ -418,34 +418,48 @@ __global__ void __launch_bounds__(256) k_tiles(const __half2* __restrict__ spec,
   // different banks (rows 4 apart are 576 bytes apart).
   const int lcv = CH == 16 ? 2 : (CH == 8 ? 1 : 0);  // CV = CH / 4 = 2^lcv
   const int nstage = S * 2 * (8 << lcv);
-  // two iterations' loads in flight per thread (the kernel is bound by the
+  // the loads of two items are issued before either item's stores, so
+  // eight 16-byte loads are in flight per thread (the kernel is bound by the
   // latency of its HBM reads)
-#pragma unroll 2
-  for (int i = tid; i < nstage; i += blockDim.x) {
+  auto decode = [&](int i, int& c, int& sb, int& b0) {
     const int b4 = i & 7;
     const int j = i >> 3;
-    const int c = 4 * (j & ((1 << lcv) - 1));
+    c = 4 * (j & ((1 << lcv) - 1));
     const int rest = j >> lcv;
-    const int bh = rest & 1;
-    const int sb = rest >> 1;
-    const int b0 = bh * 32 + b4 * 4;
-    uint4 v[4];
+    sb = rest >> 1;
+    b0 = (rest & 1) * 32 + b4 * 4;
+  };
+  for (int i0 = tid; i0 < nstage; i0 += 2 * blockDim.x) {
+    uint4 v[2][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int bg = kt * 64 + b0 + u;
-      v[u] = make_uint4(0u, 0u, 0u, 0u);
-      if (c < nch && bg < cb)
-        v[u] = __ldg(reinterpret_cast<const uint4*>(spec + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h * blockDim.x;
+      int c, sb, b0;
+      decode(i, c, sb, b0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int bg = kt * 64 + b0 + u;
+        v[h][u] = make_uint4(0u, 0u, 0u, 0u);
+        if (i < nstage && c < nch && bg < cb)
+          v[h][u] = __ldg(reinterpret_cast<const uint4*>(spec + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
+      }
     }
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      uint32_t w[4];
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h * blockDim.x;
+      if (i >= nstage) break;
+      int c, sb, b0;
+      decode(i, c, sb, b0);
 #pragma unroll
-      for (int u = 0; u < 4; ++u) w[u] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
-      const uint2 re = make_uint2((w[0] & 0xFFFFu) | (w[1] << 16), (w[2] & 0xFFFFu) | (w[3] << 16));
-      const uint2 im = make_uint2((w[0] >> 16) | (w[1] & 0xFFFF0000u), (w[2] >> 16) | (w[3] & 0xFFFF0000u));
-      *reinterpret_cast<uint2*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 2 * b0) = re;
-      *reinterpret_cast<uint2*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 2 * b0) = im;
+      for (int e = 0; e < 4; ++e) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = e == 0 ? v[h][u].x : e == 1 ? v[h][u].y : e == 2 ? v[h][u].z : v[h][u].w;
+        const uint2 re = make_uint2((w[0] & 0xFFFFu) | (w[1] << 16), (w[2] & 0xFFFFu) | (w[3] << 16));
+        const uint2 im = make_uint2((w[0] >> 16) | (w[1] & 0xFFFF0000u), (w[2] >> 16) | (w[3] & 0xFFFF0000u));
+        *reinterpret_cast<uint2*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 2 * b0) = re;
+        *reinterpret_cast<uint2*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 2 * b0) = im;
+      }
     }
   }
   __syncthreads();
@@ -467,34 +481,49 @@ __global__ void __launch_bounds__(256) k_tiles8(const uint16_t* __restrict__ spe
   const int tid = threadIdx.x;
   const int lcv = CH == 16 ? 1 : 0;  // CV = CH / 8 = 2^lcv
   const int nstage = S * (32 << lcv);
-#pragma unroll 2
-  for (int i = tid; i < nstage; i += blockDim.x) {
-    const int b4 = i & 31;
+  // two items' loads before either item's stores (eight 16-byte loads in flight)
+  auto decode = [&](int i, int& b4, int& c, int& sb) {
+    b4 = i & 31;
     const int j = i >> 5;
-    const int c = 8 * (j & ((1 << lcv) - 1));
-    const int sb = j >> lcv;
-    uint4 v[4];
+    c = 8 * (j & ((1 << lcv) - 1));
+    sb = j >> lcv;
+  };
+  for (int i0 = tid; i0 < nstage; i0 += 2 * blockDim.x) {
+    uint4 v[2][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int bg = kt * 128 + 4 * b4 + u;
-      v[u] = make_uint4(0u, 0u, 0u, 0u);
-      if (c < nch && bg < cb)
-        v[u] = __ldg(reinterpret_cast<const uint4*>(spec8 + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
-    }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      uint32_t w[4];
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h * blockDim.x;
+      int b4, c, sb;
+      decode(i, b4, c, sb);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int q = e >> 1;
-        w[u] = q == 0 ? v[u].x : q == 1 ? v[u].y : q == 2 ? v[u].z : v[u].w;
+        const int bg = kt * 128 + 4 * b4 + u;
+        v[h][u] = make_uint4(0u, 0u, 0u, 0u);
+        if (i < nstage && c < nch && bg < cb)
+          v[h][u] = __ldg(reinterpret_cast<const uint4*>(spec8 + (((size_t)jo * CB + bg) * S + sb) * (size_t)nchan + c0 + c));
       }
-      // channel e sits in bytes 0,1 (even e) or 2,3 (odd e) of its word
-      const uint32_t sre = (e & 1) ? 0x0062u : 0x0040u, sim = (e & 1) ? 0x0073u : 0x0051u;
-      const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], sre), __byte_perm(w[2], w[3], sre), 0x5410);
-      const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], sim), __byte_perm(w[2], w[3], sim), 0x5410);
-      *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 4 * b4) = re;
-      *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 4 * b4) = im;
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h * blockDim.x;
+      if (i >= nstage) break;
+      int b4, c, sb;
+      decode(i, b4, c, sb);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = e >> 1;
+          w[u] = q == 0 ? v[h][u].x : q == 1 ? v[h][u].y : q == 2 ? v[h][u].z : v[h][u].w;
+        }
+        // channel e sits in bytes 0,1 (even e) or 2,3 (odd e) of its word
+        const uint32_t sre = (e & 1) ? 0x0062u : 0x0040u, sim = (e & 1) ? 0x0073u : 0x0051u;
+        const uint32_t re = __byte_perm(__byte_perm(w[0], w[1], sre), __byte_perm(w[2], w[3], sre), 0x5410);
+        const uint32_t im = __byte_perm(__byte_perm(w[0], w[1], sim), __byte_perm(w[2], w[3], sim), 0x5410);
+        *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 4 * b4) = re;
+        *reinterpret_cast<uint32_t*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 4 * b4) = im;
+      }
     }
   }
   __syncthreads();

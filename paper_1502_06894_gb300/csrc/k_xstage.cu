@@ -29,6 +29,10 @@ __device__ __forceinline__ float2 cmac_conj(float2 acc, float2 x, float2 xr, flo
   return __ffma2_rn(xr, make_float2(y.y, y.y), __ffma2_rn(x, make_float2(y.x, y.x), acc));
 }
 __device__ __forceinline__ float2 rot_conj(float2 x) { return __fmul2_rn(make_float2(x.y, x.x), make_float2(1.f, -1.f)); }
+// An autocorrelation needs only |x|^2: the accumulator keeps (sum re^2,
+// sum im^2), one f32x2 FMA per block; auto_value() forms the visibility.
+__device__ __forceinline__ float2 cmac_auto(float2 acc, float2 x) { return __ffma2_rn(x, x, acc); }
+__device__ __forceinline__ float2 auto_value(float2 acc) { return make_float2(acc.x + acc.y, 0.f); }
 
 template <int TA, bool DIAG>
 __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
@@ -76,7 +80,9 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     for (int i = 0; i < TA; ++i) {
       const float2 ar = rot_conj(a[i]);
 #pragma unroll
-      for (int j = DIAG ? i : 0; j < TA; ++j) acc[i][j] = cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
+      for (int j = DIAG ? i : 0; j < TA; ++j)
+        acc[i][j] = (DIAG && j == i) ? cmac_auto(acc[i][j], a[i])
+                                     : cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
     }
   }
   const int nbl = nbl_of(S);
@@ -87,9 +93,10 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
       const int sa = ta * TA + i, sb = tb * TA + j;
       if (sa < S && sb < S) {
         float2* dst = p.part + (((size_t)kz * nbl + bl_index(sa, sb, S)) * p.G + g) * sstride + k;
+        const float2 x = (DIAG && j == i) ? auto_value(acc[i][j]) : acc[i][j];
         float2 v = *dst;
-        v.x += acc[i][j].x;
-        v.y += acc[i][j].y;
+        v.x += x.x;
+        v.y += x.y;
         *dst = v;
       }
     }
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
       for (int i = 0; i < TA; ++i) {
         const float2 ar = rot_conj(a[i]);
 #pragma unroll
-        for (int j = i; j < TA; ++j) acc[i][j] = cmac_conj(acc[i][j], a[i], ar, a[j]);
+        for (int j = i; j < TA; ++j) acc[i][j] = j == i ? cmac_auto(acc[i][j], a[i]) : cmac_conj(acc[i][j], a[i], ar, a[j]);
       }
     }
     __syncthreads();
@@ -184,8 +191,12 @@ __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
         // one add per element per launch: deterministic fire-and-forget reduction
         float* dst = reinterpret_cast<float*>(p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) *
                                                            (size_t)p.nchan + k);
-        atomicAdd(dst, acc[i][j].x);
-        atomicAdd(dst + 1, acc[i][j].y);
+        if (j == i) {
+          atomicAdd(dst, auto_value(acc[i][j]).x);
+        } else {
+          atomicAdd(dst, acc[i][j].x);
+          atomicAdd(dst + 1, acc[i][j].y);
+        }
       }
 }
 
@@ -324,7 +335,8 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
         for (int i = I0; i < I1; ++i) {
           const float2 ar = rot_conj(a[i]);
 #pragma unroll
-          for (int j = i; j < TA; ++j) acc[i][j] = cmac_conj(acc[i][j], a[i], ar, a[j]);
+          for (int j = i; j < TA; ++j)
+            acc[i][j] = j == i ? cmac_auto(acc[i][j], a[i]) : cmac_conj(acc[i][j], a[i], ar, a[j]);
         }
       }
       __syncthreads();
@@ -356,8 +368,12 @@ __global__ void __launch_bounds__(kXThreadsT) k_xmac_tma(const __grid_constant__
         if (i < S && j < S) {
           float* dst = reinterpret_cast<float*>(p.part + (((size_t)kz * nbl + bl_index(i, j, S)) * p.G + g) *
                                                              (size_t)p.nchan + k);
-          atomicAdd(dst, acc[i][j].x);
-          atomicAdd(dst + 1, acc[i][j].y);
+          if (j == i) {
+            atomicAdd(dst, auto_value(acc[i][j]).x);
+          } else {
+            atomicAdd(dst, acc[i][j].x);
+            atomicAdd(dst + 1, acc[i][j].y);
+          }
         }
   };
   constexpr int SPLIT = tri_split(TA, 2, 1);

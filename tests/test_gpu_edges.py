@@ -183,3 +183,33 @@ def test_ragged_integrations_and_data_edges(corr):
         err = rel_rms_per_baseline(v[nz], ref[i][nz])
         assert np.all(err < 1e-5), (i, err.max())
         assert np.all(v[~nz] == 0)
+
+
+@pytest.mark.parametrize("S,nchan,nsub,npol,chunk", [
+    (17, 256, 1, 2, 0),    # 3 tile pairs: 32 channels per CTA
+    (40, 128, 1, 1, 0),    # 15 tile pairs: 16 channels per CTA
+    (50, 64, 2, 1, 24),    # 28 tile pairs: 8 channels per CTA, forced chunks
+    (64, 256, 1, 1, 0),    # 36 tile pairs: 4 channels per CTA (the dense FP32 shape)
+    (64, 4, 1, 1, 0),      # fewer channels than a CTA takes
+])
+def test_fp32_x_step_above_12_stations(corr, S, nchan, nsub, npol, chunk):
+    """The FP32 X step for more than 12 stations (every station's values of
+    a CTA's channels staged once in shared memory, 8 x 8 tile pairs per
+    thread): all tile-pair counts and channel widths, ragged integrations of
+    about 40 blocks, against the oracle within 1e-5 and with exact weights."""
+    fs = 32e6
+    N = 2 * nchan
+    tint = round((40 * N + 7) / fs * fs) / fs
+    sc = synth.config2(seed=S * 7 + nchan, duration=2 * tint, tint=tint, boundary=tint, nchan=nchan, stations=S,
+                       nsub=nsub, npol=npol)
+    streams = [synth.station_bytes(sc, s, physics=False) for s in range(S)]
+    ref, wref = oracle.Oracle.from_scan(sc, streams).correlate(0, 2)
+    c = corr.from_scan(sc, streams)
+    if chunk:
+        c.set_chunk_blocks(chunk)
+    vis, w = correlate_n(c, 2)
+    c.close()
+    assert np.array_equal(w, wref)
+    for i in range(2):
+        err = rel_rms_per_baseline(vis[i].reshape(sc.nbl, sc.G, sc.nchan), ref[i])
+        assert np.all(err < TOL[0]), (i, err.max())
