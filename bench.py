@@ -501,7 +501,7 @@ def batch_leg(args, torch, corr, dev):
     """96 uneven scans (2-20 stations, 1-16 subbands, 1-2 pols, 128-8192
     channels, 0.5-30 s): all admitted at once and advanced one integration per
     step, every step one CUDA graph over all open scans, chunk lengths from
-    the autotuner, FP16 spectra (X unit chosen per scan by CORR_X_AUTO).  Compared with the same scans one
+    the autotuner, FP16 spectra (chunk length and X unit chosen per shape by the autotuner).  Compared with the same scans one
     after another through corr_correlate_device (same precision and chunks),
     and with plain FP32 one after another at the library's default chunks.
     Samples come from a device-resident pool that every station reads at its
@@ -543,7 +543,11 @@ def batch_leg(args, torch, corr, dev):
             "serial_fp32": {"value": samples / t_fp32, "seconds": t_fp32},
             "batched_vs_per_scan": t_scan / t_batch, "batched_tc_vs_serial_fp32": t_fp32 / t_batch,
             "autotune": {"seconds": tune_s, "trials": tuner.trials, "shapes": len(tuner.cache),
-                         "chunk_blocks_chosen": sorted(set(tuner.cache.values()))},
+                         "chunk_blocks_chosen": sorted(set(v[0] for v in tuner.cache.values())),
+                         "x_unit_chosen": {"cuda_cores": sum(1 for v in tuner.cache.values()
+                                                             if v[1] == corr.CORR_X_CUDA_CORES),
+                                           "tensor_cores": sum(1 for v in tuner.cache.values()
+                                                               if v[1] == corr.CORR_X_TENSOR_CORES)}},
             "timing": "wall clock around the whole run, synchronised, handle set-up included",
             "data": "device-resident random 2-bit pool, per-station offsets (replayed chunk)"}
 

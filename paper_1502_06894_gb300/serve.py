@@ -226,7 +226,8 @@ class ReplayPool:
 
 
 class Autotuner:
-    """Chooses the F/X chunk length (spectra blocks per chunk) per scan shape
+    """Chooses the F/X chunk length (spectra blocks per chunk) and, for the
+    FP16 / FP8 modes, the X unit (CUDA cores or tensor cores) per scan shape
     by timing one integration per candidate with CUDA events, within a device
     memory cap per job.  Results are cached per (stations, streams, channels,
     blocks per integration, precision)."""
@@ -238,7 +239,7 @@ class Autotuner:
         self.pool = pool
         self.dev = device
         self.mem_cap = int(mem_cap)
-        self.cache: Dict[tuple, int] = {}
+        self.cache: Dict[tuple, tuple] = {}  # key -> (chunk blocks, X unit)
         self.trials = 0
 
     def key(self, scan, precision):
@@ -246,18 +247,29 @@ class Autotuner:
         return (scan.stations, scan.nsub * scan.npol, scan.nchan, blocks, precision)
 
     def choose(self, scan, precision) -> int:
+        """Chunk length for the scan's shape (tuned on first use)."""
+        return self.config(scan, precision)[0]
+
+    def x_unit(self, scan, precision) -> int:
+        """X unit for the scan's shape (tuned on first use)."""
+        return self.config(scan, precision)[1]
+
+    def config(self, scan, precision) -> tuple:
         import torch
         k = self.key(scan, precision)
         if k in self.cache:
             return self.cache[k]
         blocks = k[3] + 1
         cands = sorted({min(c, blocks) for c in self.CANDIDATES})
-        best, best_ms = cands[0], None
+        units = (self.corr.CORR_X_AUTO,) if precision == self.corr.CORR_PREC_FP32 else \
+            (self.corr.CORR_X_CUDA_CORES, self.corr.CORR_X_TENSOR_CORES)
+        best, best_ms = (cands[0], units[0]), None
         out = torch.empty((scan.nbl, scan.nsub * scan.npol, scan.nchan), dtype=torch.complex64, device=self.dev)
-        for cb in cands:
+        for cb, unit in [(cb, u) for cb in cands for u in units]:
             c = self.corr.from_scan(scan)
             try:
                 c.set_precision(precision)
+                c.set_x_unit(unit)
                 c.set_chunk_blocks(cb)
                 if c.device_bytes() + out.numel() * 8 > self.mem_cap and cb != cands[0]:
                     continue
@@ -277,7 +289,7 @@ class Autotuner:
                     continue
                 ms = e0.elapsed_time(e1)
                 if best_ms is None or ms < best_ms:
-                    best, best_ms = cb, ms
+                    best, best_ms = (cb, unit), ms
             finally:
                 c.close()
         self.cache[k] = best
@@ -312,7 +324,8 @@ class GpuExecutor:
         c.set_precision(job.precision if job.precision is not None else self.precision)
         cb = self.chunk_blocks
         if cb is None and self.tuner is not None:
-            cb = self.tuner.choose(job.scan, job.precision)
+            cb, unit = self.tuner.config(job.scan, job.precision)
+            c.set_x_unit(unit)
         if cb:
             c.set_chunk_blocks(cb)
         return c
