@@ -34,20 +34,24 @@ __device__ __forceinline__ float2 rot_conj(float2 x) { return __fmul2_rn(make_fl
 __device__ __forceinline__ float2 cmac_auto(float2 acc, float2 x) { return __ffma2_rn(x, x, acc); }
 __device__ __forceinline__ float2 auto_value(float2 acc) { return make_float2(acc.x + acc.y, 0.f); }
 
+// The tile pairs of one 128-channel tile are consecutive CTAs (blockIdx.x
+// = channel tile x pairs + pair), so the pairs that read the same stations'
+// spectra run side by side and all but the first read come from L2.  The
+// diagonal pairs (DIAG) and the off-diagonal ones are separate launches.
 template <int TA, bool DIAG>
 __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
-  const int k = blockIdx.x * kXT + threadIdx.x;
+  const int npo = DIAG ? ntile : ntile * (ntile - 1) / 2;  // pairs of this launch
+  const int pidx = blockIdx.x % npo;
+  const int k = (blockIdx.x / npo) * kXT + threadIdx.x;
   const int g = blockIdx.y;
-  const int npairs = ntile * (ntile + 1) / 2;
-  const int pair = blockIdx.z % npairs;
-  const int kz = blockIdx.z / npairs;
-  int ta = 0, tb = 0;
-  {
-    int q = pair;
-    while (q >= ntile - ta) { q -= ntile - ta; ++ta; }
-    tb = ta + q;
+  const int kz = blockIdx.z;
+  int ta = pidx, tb = pidx;
+  if (!DIAG) {  // off-diagonal pair pidx in row-major order over ta < tb
+    int q = pidx;
+    ta = 0;
+    while (q >= ntile - 1 - ta) { q -= ntile - 1 - ta; ++ta; }
+    tb = ta + 1 + q;
   }
-  if (DIAG != (ta == tb)) return;
   if (k >= p.nchan) return;
   const int S = p.S;
   const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
@@ -61,9 +65,11 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   const size_t sstride = (size_t)p.nchan;
-  for (int bb = b_lo; bb < b_hi; ++bb) {
+  // the values of block bb + 1 are loaded while block bb is accumulated (two
+  // register sets in turn): with 8 warps per SM the load latency would
+  // otherwise stall the FMAs
+  auto load = [&](int bb, float2 (&a)[TA], float2 (&b)[TA]) {
     const float2* base = p.spec + ((size_t)g * p.CB + bb) * (size_t)S * sstride + k;
-    float2 a[TA], b[TA];
 #pragma unroll
     for (int i = 0; i < TA; ++i) {
       const int sa = ta * TA + i;
@@ -76,6 +82,8 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
         b[i] = sb < S ? __ldg(base + sb * sstride) : make_float2(0.f, 0.f);
       }
     }
+  };
+  auto mac = [&](const float2 (&a)[TA], const float2 (&b)[TA]) {
 #pragma unroll
     for (int i = 0; i < TA; ++i) {
       const float2 ar = rot_conj(a[i]);
@@ -84,6 +92,15 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
         acc[i][j] = (DIAG && j == i) ? cmac_auto(acc[i][j], a[i])
                                      : cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
     }
+  };
+  float2 a0[TA], b0[TA], a1[TA], b1[TA];
+  load(b_lo, a0, b0);
+  for (int bb = b_lo; bb < b_hi; bb += 2) {
+    if (bb + 1 < b_hi) load(bb + 1, a1, b1);
+    mac(a0, b0);
+    if (bb + 1 >= b_hi) break;
+    if (bb + 2 < b_hi) load(bb + 2, a0, b0);
+    mac(a1, b1);
   }
   const int nbl = nbl_of(S);
 #pragma unroll
@@ -480,13 +497,12 @@ static cudaError_t launch_ring(const XParams& p, cudaStream_t s) {
 template <int TA>
 static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
   const int nt = (p.S + TA - 1) / TA;
-  const int npairs = nt * (nt + 1) / 2;
-  dim3 grid((p.nchan + kXT - 1) / kXT, p.G, npairs * p.KZ);
-  k_xmac<TA, true><<<grid, kXT, 0, s>>>(p, nt);
+  const int ntiles = (p.nchan + kXT - 1) / kXT;
+  k_xmac<TA, true><<<dim3(nt * ntiles, p.G, p.KZ), kXT, 0, s>>>(p, nt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || nt == 1) return e;
   if constexpr (TA == 8) {  // only the 8-station tiling has off-diagonal tiles
-    k_xmac<TA, false><<<grid, kXT, 0, s>>>(p, nt);
+    k_xmac<TA, false><<<dim3(nt * (nt - 1) / 2 * ntiles, p.G, p.KZ), kXT, 0, s>>>(p, nt);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
