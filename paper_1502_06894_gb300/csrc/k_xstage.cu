@@ -22,6 +22,11 @@ namespace corr {
 
 constexpr int kXT = 128;  // threads per CTA (channels)
 
+// 16-byte asynchronous copy to shared memory; src_bytes = 0 writes zeros.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+
 // acc + x conj(y) on packed FP32 pairs: acc + x (y.x, y.x) + xr (y.y, y.y)
 // with xr = (x.y, -x.x), formed once per loaded value: two f32x2 fused
 // multiply-adds per baseline instead of four scalar ones.
@@ -38,11 +43,20 @@ __device__ __forceinline__ float2 auto_value(float2 acc) { return make_float2(ac
 // = channel tile x pairs + pair), so the pairs that read the same stations'
 // spectra run side by side and all but the first read come from L2.  The
 // diagonal pairs (DIAG) and the off-diagonal ones are separate launches.
+// The 2 x 8 stations' values of each block reach shared memory through a
+// cp.async ring of kStagesT blocks, so that many blocks' loads are in flight
+// without registers (the accumulators take 128 of them).
+constexpr int kStagesT = 4;
+
 template <int TA, bool DIAG>
 __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
+  extern __shared__ __align__(16) unsigned char xt_raw[];
+  constexpr int NT = DIAG ? 1 : 2;                 // station tiles per block
+  float2* ring = reinterpret_cast<float2*>(xt_raw);  // [kStagesT][NT][TA][kXT]
   const int npo = DIAG ? ntile : ntile * (ntile - 1) / 2;  // pairs of this launch
   const int pidx = blockIdx.x % npo;
-  const int k = (blockIdx.x / npo) * kXT + threadIdx.x;
+  const int k0 = (blockIdx.x / npo) * kXT;
+  const int k = k0 + threadIdx.x;
   const int g = blockIdx.y;
   const int kz = blockIdx.z;
   int ta = pidx, tb = pidx;
@@ -52,11 +66,36 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     while (q >= ntile - 1 - ta) { q -= ntile - 1 - ta; ++ta; }
     tb = ta + 1 + q;
   }
-  if (k >= p.nchan) return;
   const int S = p.S;
   const int b_lo = (int)((int64_t)p.CB * kz / p.KZ);
   const int b_hi = (int)((int64_t)p.CB * (kz + 1) / p.KZ);
   if (b_hi <= b_lo) return;
+  const int nb = b_hi - b_lo;
+  constexpr int stage_elems = NT * TA * kXT;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  const size_t sstride = (size_t)p.nchan;
+
+  // copies of block b_lo + q into slot q % kStagesT: NT x TA rows of 128
+  // channels, 64 pieces of 16 bytes each; rows beyond S and channels beyond
+  // nchan are zero-filled
+  auto issue = [&](int q) {
+    if (q < nb) {
+      const int slot = q % kStagesT;
+      const int b = b_lo + q;
+      for (int e = threadIdx.x; e < NT * TA * 64; e += kXT) {
+        const int piece = e & 63;
+        const int row = e >> 6;                     // (tile, station in tile)
+        const int st = ((row >= TA) ? tb : ta) * TA + (row % TA);
+        const int ch = k0 + piece * 2;
+        const bool in = st < S && ch < p.nchan;
+        const float2* src = p.spec + ((size_t)g * p.CB + b) * (size_t)S * sstride + (size_t)(in ? st : 0) * sstride +
+                            (in ? ch : 0);
+        const uint32_t dst = ring_s + (uint32_t)((slot * stage_elems + row * kXT + piece * 2) * 8);
+        cp_async16(dst, src, in ? 16 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
 
   float2 acc[TA][TA];
 #pragma unroll
@@ -64,26 +103,19 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
 #pragma unroll
     for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  const size_t sstride = (size_t)p.nchan;
-  // the values of block bb + 1 are loaded while block bb is accumulated (two
-  // register sets in turn): with 8 warps per SM the load latency would
-  // otherwise stall the FMAs
-  auto load = [&](int bb, float2 (&a)[TA], float2 (&b)[TA]) {
-    const float2* base = p.spec + ((size_t)g * p.CB + bb) * (size_t)S * sstride + k;
+  for (int q = 0; q < kStagesT - 1; ++q) issue(q);
+  for (int q = 0; q < nb; ++q) {
+    issue(q + kStagesT - 1);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kStagesT - 1) : "memory");
+    __syncthreads();
+    const float2* st = ring + (q % kStagesT) * stage_elems + threadIdx.x;
+    float2 a[TA], b[TA];
 #pragma unroll
-    for (int i = 0; i < TA; ++i) {
-      const int sa = ta * TA + i;
-      a[i] = sa < S ? __ldg(base + sa * sstride) : make_float2(0.f, 0.f);
-    }
+    for (int i = 0; i < TA; ++i) a[i] = st[i * kXT];
     if (!DIAG) {
 #pragma unroll
-      for (int i = 0; i < TA; ++i) {
-        const int sb = tb * TA + i;
-        b[i] = sb < S ? __ldg(base + sb * sstride) : make_float2(0.f, 0.f);
-      }
+      for (int i = 0; i < TA; ++i) b[i] = st[(TA + i) * kXT];
     }
-  };
-  auto mac = [&](const float2 (&a)[TA], const float2 (&b)[TA]) {
 #pragma unroll
     for (int i = 0; i < TA; ++i) {
       const float2 ar = rot_conj(a[i]);
@@ -92,16 +124,10 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
         acc[i][j] = (DIAG && j == i) ? cmac_auto(acc[i][j], a[i])
                                      : cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
     }
-  };
-  float2 a0[TA], b0[TA], a1[TA], b1[TA];
-  load(b_lo, a0, b0);
-  for (int bb = b_lo; bb < b_hi; bb += 2) {
-    if (bb + 1 < b_hi) load(bb + 1, a1, b1);
-    mac(a0, b0);
-    if (bb + 1 >= b_hi) break;
-    if (bb + 2 < b_hi) load(bb + 2, a0, b0);
-    mac(a1, b1);
+    __syncthreads();
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (k >= p.nchan) return;
   const int nbl = nbl_of(S);
 #pragma unroll
   for (int i = 0; i < TA; ++i)
@@ -127,9 +153,6 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
 constexpr int kNB = 2;       // blocks per stage
 constexpr int kStagesX = 4;  // ring depth
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
-}
 
 template <int TA>
 __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
@@ -498,11 +521,16 @@ template <int TA>
 static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
   const int nt = (p.S + TA - 1) / TA;
   const int ntiles = (p.nchan + kXT - 1) / kXT;
-  k_xmac<TA, true><<<dim3(nt * ntiles, p.G, p.KZ), kXT, 0, s>>>(p, nt);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || nt == 1) return e;
+  const size_t smem1 = (size_t)kStagesT * TA * kXT * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(k_xmac<TA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+  if (e != cudaSuccess) return e;
+  k_xmac<TA, true><<<dim3(nt * ntiles, p.G, p.KZ), kXT, smem1, s>>>(p, nt);
+  if ((e = cudaGetLastError()) != cudaSuccess || nt == 1) return e;
   if constexpr (TA == 8) {  // only the 8-station tiling has off-diagonal tiles
-    k_xmac<TA, false><<<dim3(nt * (nt - 1) / 2 * ntiles, p.G, p.KZ), kXT, 0, s>>>(p, nt);
+    const size_t smem2 = 2 * smem1;
+    e = cudaFuncSetAttribute(k_xmac<TA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    k_xmac<TA, false><<<dim3(nt * (nt - 1) / 2 * ntiles, p.G, p.KZ), kXT, smem2, s>>>(p, nt);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
