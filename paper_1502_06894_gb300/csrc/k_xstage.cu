@@ -46,17 +46,36 @@ __device__ __forceinline__ float2 auto_value(float2 acc) { return make_float2(ac
 // The 2 x 8 stations' values of each block reach shared memory through a
 // cp.async ring of kStagesT blocks, so that many blocks' loads are in flight
 // without registers (the accumulators take 128 of them).
+// First tile row of part `part` of `npart` for a triangular tile: the parts
+// get about equal numbers of baselines (row i holds TA - i of them).
+__host__ __device__ constexpr int tri_split(int TA, int npart, int part) {
+  if (part <= 0) return 0;
+  if (part >= npart) return TA;
+  int acc = 0, i = 0;
+  const int total = TA * (TA + 1) / 2;
+  while (i < TA && 2 * npart * (acc + (TA - i)) <= 2 * total * part + npart * (TA - i)) {
+    acc += TA - i;
+    ++i;
+  }
+  return i;
+}
+
 constexpr int kStagesT = 4;
 
+// Two threads per channel: thread part 0 takes tile rows [0, SPLIT) and
+// part 1 rows [SPLIT, TA) (half the baselines each), so a thread holds 32
+// accumulators instead of 64 and an SM runs twice the warps.
 template <int TA, bool DIAG>
-__global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
+__global__ void __launch_bounds__(2 * kXT) k_xmac(XParams p, int ntile) {
   extern __shared__ __align__(16) unsigned char xt_raw[];
   constexpr int NT = DIAG ? 1 : 2;                 // station tiles per block
   float2* ring = reinterpret_cast<float2*>(xt_raw);  // [kStagesT][NT][TA][kXT]
   const int npo = DIAG ? ntile : ntile * (ntile - 1) / 2;  // pairs of this launch
   const int pidx = blockIdx.x % npo;
   const int k0 = (blockIdx.x / npo) * kXT;
-  const int k = k0 + threadIdx.x;
+  const int lane = threadIdx.x % kXT;
+  const int part = threadIdx.x / kXT;
+  const int k = k0 + lane;
   const int g = blockIdx.y;
   const int kz = blockIdx.z;
   int ta = pidx, tb = pidx;
@@ -82,7 +101,7 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     if (q < nb) {
       const int slot = q % kStagesT;
       const int b = b_lo + q;
-      for (int e = threadIdx.x; e < NT * TA * 64; e += kXT) {
+      for (int e = threadIdx.x; e < NT * TA * 64; e += 2 * kXT) {
         const int piece = e & 63;
         const int row = e >> 6;                     // (tile, station in tile)
         const int st = ((row >= TA) ? tb : ta) * TA + (row % TA);
@@ -97,52 +116,60 @@ __global__ void __launch_bounds__(kXT) k_xmac(XParams p, int ntile) {
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
 
-  float2 acc[TA][TA];
+  auto run = [&](auto I0c, auto I1c) {
+    constexpr int I0 = decltype(I0c)::value, I1 = decltype(I1c)::value;
+    float2 acc[TA][TA];
 #pragma unroll
-  for (int i = 0; i < TA; ++i)
+    for (int i = I0; i < I1; ++i)
 #pragma unroll
-    for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
+      for (int j = 0; j < TA; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
-  for (int q = 0; q < kStagesT - 1; ++q) issue(q);
-  for (int q = 0; q < nb; ++q) {
-    issue(q + kStagesT - 1);
-    asm volatile("cp.async.wait_group %0;" ::"n"(kStagesT - 1) : "memory");
-    __syncthreads();
-    const float2* st = ring + (q % kStagesT) * stage_elems + threadIdx.x;
-    float2 a[TA], b[TA];
+    for (int q = 0; q < kStagesT - 1; ++q) issue(q);
+    for (int q = 0; q < nb; ++q) {
+      issue(q + kStagesT - 1);
+      asm volatile("cp.async.wait_group %0;" ::"n"(kStagesT - 1) : "memory");
+      __syncthreads();
+      const float2* st = ring + (q % kStagesT) * stage_elems + lane;
+      float2 a[TA], b[TA];
 #pragma unroll
-    for (int i = 0; i < TA; ++i) a[i] = st[i * kXT];
-    if (!DIAG) {
+      for (int i = I0; i < (DIAG ? TA : I1); ++i) a[i] = st[i * kXT];
+      if (!DIAG) {
 #pragma unroll
-      for (int i = 0; i < TA; ++i) b[i] = st[(TA + i) * kXT];
-    }
-#pragma unroll
-    for (int i = 0; i < TA; ++i) {
-      const float2 ar = rot_conj(a[i]);
-#pragma unroll
-      for (int j = DIAG ? i : 0; j < TA; ++j)
-        acc[i][j] = (DIAG && j == i) ? cmac_auto(acc[i][j], a[i])
-                                     : cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
-    }
-    __syncthreads();
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  if (k >= p.nchan) return;
-  const int nbl = nbl_of(S);
-#pragma unroll
-  for (int i = 0; i < TA; ++i)
-#pragma unroll
-    for (int j = DIAG ? i : 0; j < TA; ++j) {
-      const int sa = ta * TA + i, sb = tb * TA + j;
-      if (sa < S && sb < S) {
-        float2* dst = p.part + (((size_t)kz * nbl + bl_index(sa, sb, S)) * p.G + g) * sstride + k;
-        const float2 x = (DIAG && j == i) ? auto_value(acc[i][j]) : acc[i][j];
-        float2 v = *dst;
-        v.x += x.x;
-        v.y += x.y;
-        *dst = v;
+        for (int i = 0; i < TA; ++i) b[i] = st[(TA + i) * kXT];
       }
+#pragma unroll
+      for (int i = I0; i < I1; ++i) {
+        const float2 ar = rot_conj(a[i]);
+#pragma unroll
+        for (int j = DIAG ? i : 0; j < TA; ++j)
+          acc[i][j] = (DIAG && j == i) ? cmac_auto(acc[i][j], a[i])
+                                       : cmac_conj(acc[i][j], a[i], ar, DIAG ? a[j] : b[j]);  // X_a conj(X_b)
+      }
+      __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (k >= p.nchan) return;
+    const int nbl = nbl_of(S);
+#pragma unroll
+    for (int i = I0; i < I1; ++i)
+#pragma unroll
+      for (int j = DIAG ? i : 0; j < TA; ++j) {
+        const int sa = ta * TA + i, sb = tb * TA + j;
+        if (sa < S && sb < S) {
+          float2* dst = p.part + (((size_t)kz * nbl + bl_index(sa, sb, S)) * p.G + g) * sstride + k;
+          const float2 x = (DIAG && j == i) ? auto_value(acc[i][j]) : acc[i][j];
+          float2 v = *dst;
+          v.x += x.x;
+          v.y += x.y;
+          *dst = v;
+        }
+      }
+  };
+  constexpr int SPLIT = DIAG ? tri_split(TA, 2, 1) : TA / 2;
+  if (part == 0)
+    run(std::integral_constant<int, 0>{}, std::integral_constant<int, SPLIT>{});
+  else
+    run(std::integral_constant<int, SPLIT>{}, std::integral_constant<int, TA>{});
 }
 
 // For S <= 12 (one triangular tile of baselines per channel) the spectra
@@ -246,20 +273,6 @@ __global__ void __launch_bounds__(kXT) k_xmac_ring(XParams p) {
 // limited by per-thread outstanding requests.  Thread 0 issues the copies; an
 // mbarrier with a transaction count per ring slot signals arrival; every wait
 // is bounded (timeout -> *err, the CTA stops issuing and returns).
-// First tile row of part `part` of `npart` for a triangular tile: the parts
-// get about equal numbers of baselines (row i holds TA - i of them).
-__host__ __device__ constexpr int tri_split(int TA, int npart, int part) {
-  if (part <= 0) return 0;
-  if (part >= npart) return TA;
-  int acc = 0, i = 0;
-  const int total = TA * (TA + 1) / 2;
-  while (i < TA && 2 * npart * (acc + (TA - i)) <= 2 * total * part + npart * (TA - i)) {
-    acc += TA - i;
-    ++i;
-  }
-  return i;
-}
-
 constexpr long long kXDrainLimit = 1LL << 26;  // spins per wait while draining after an abort
 
 __device__ __forceinline__ uint32_t xs_u32(const void* ptr) { return (uint32_t)__cvta_generic_to_shared(ptr); }
@@ -524,13 +537,13 @@ static cudaError_t launch_TA(const XParams& p, cudaStream_t s) {
   const size_t smem1 = (size_t)kStagesT * TA * kXT * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(k_xmac<TA, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
   if (e != cudaSuccess) return e;
-  k_xmac<TA, true><<<dim3(nt * ntiles, p.G, p.KZ), kXT, smem1, s>>>(p, nt);
+  k_xmac<TA, true><<<dim3(nt * ntiles, p.G, p.KZ), 2 * kXT, smem1, s>>>(p, nt);
   if ((e = cudaGetLastError()) != cudaSuccess || nt == 1) return e;
   if constexpr (TA == 8) {  // only the 8-station tiling has off-diagonal tiles
     const size_t smem2 = 2 * smem1;
     e = cudaFuncSetAttribute(k_xmac<TA, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     if (e != cudaSuccess) return e;
-    k_xmac<TA, false><<<dim3(nt * (nt - 1) / 2 * ntiles, p.G, p.KZ), kXT, smem2, s>>>(p, nt);
+    k_xmac<TA, false><<<dim3(nt * (nt - 1) / 2 * ntiles, p.G, p.KZ), 2 * kXT, smem2, s>>>(p, nt);
     return cudaGetLastError();
   }
   return cudaErrorInvalidValue;
