@@ -25,6 +25,7 @@
 
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <atomic>
 
 namespace corr {
@@ -387,7 +388,7 @@ __device__ __forceinline__ void write_staged_rows(const unsigned char* turn_raw,
   const int per = CH * 8;                  // (channel, chunk) pairs; CH * 8 divides the 256 threads
   const int comb = threadIdx.x & (per - 1);
   const int c = comb >> 3, kc = comb & 7;
-  if (c >= nch) return;
+  if (c >= nch) return;  // no barrier follows in any caller
   const int k = c0 + c;
   const int sl = k / o.W;
   const int cw = k - sl * o.W;
@@ -530,9 +531,112 @@ __global__ void __launch_bounds__(256) k_tiles8(const uint16_t* __restrict__ spe
   write_staged_rows(turn_raw, o, S, nch, CH, c0, kt, jo);
 }
 
+// Persistent FP16 corner turn: each CTA walks work items (channel group,
+// K tile, stream); item i+1's spectra are copied with cp.async into the
+// other half of a double-buffered raw stage ([station][block][CH] as 16-byte
+// pieces of 4 channels) while item i is rearranged from the raw stage into
+// the staged tile rows and written, so that the HBM reads of one item
+// overlap the rearrangement and the writes of the one before.
+__global__ void __launch_bounds__(256, 1) k_tiles_p(const __half2* __restrict__ spec, TcTiles o, int CB, int cb,
+                                                   int S, int nchan, int CH, int ngroups, int nitems) {
+  extern __shared__ __align__(16) unsigned char tp_raw[];
+  const int PPR = CH / 4;                                  // 16-byte pieces per (station, block)
+  const int raw_pieces = S * 64 * PPR;                     // per raw buffer
+  uint4* raw = reinterpret_cast<uint4*>(tp_raw);           // [2][S][64][PPR]
+  unsigned char* turn_raw = tp_raw + (size_t)2 * raw_pieces * 16;  // [Re/Im][S][CH] rows of kTurnRow bytes
+  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(raw);
+  const int tid = threadIdx.x;
+  auto decode_item = [&](int it, int& c0, int& kt, int& jo) {
+    const int cg = it % ngroups;
+    const int rest = it / ngroups;
+    c0 = cg * CH;
+    kt = rest % o.NKT;
+    jo = rest / o.NKT;
+  };
+  auto issue = [&](int it, int buf) {
+    if (it < nitems) {
+      int c0, kt, jo;
+      decode_item(it, c0, kt, jo);
+      for (int e = tid; e < raw_pieces; e += blockDim.x) {
+        const int q = e % PPR;
+        const int row = e / PPR;                           // sb * 64 + block
+        const int blk = row & 63;
+        const int sb = row >> 6;
+        const int bg = kt * 64 + blk;
+        const int c = c0 + 4 * q;
+        const bool in = bg < cb && c < nchan;
+        const __half2* src = spec + (((size_t)jo * CB + (in ? bg : 0)) * S + sb) * (size_t)nchan + (in ? c : 0);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(raw_s + (uint32_t)((buf * raw_pieces + e) * 16)),
+                     "l"(src), "r"(in ? 16 : 0));
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const int lcv = CH == 16 ? 2 : (CH == 8 ? 1 : 0);        // CV = CH / 4 = 2^lcv
+  const int nstage = S * 2 * (8 << lcv);
+  int buf = 0;
+  issue(blockIdx.x, 0);
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x, buf ^= 1) {
+    issue(it + gridDim.x, buf ^ 1);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncthreads();  // raw[buf] has landed; the previous item's rows are written
+    int c0, kt, jo;
+    decode_item(it, c0, kt, jo);
+    const int nch = min(CH, nchan - c0);
+    const uint4* rb = raw + buf * raw_pieces;
+    for (int i = tid; i < nstage; i += blockDim.x) {
+      const int b4 = i & 7;
+      const int j = i >> 3;
+      const int c = 4 * (j & ((1 << lcv) - 1));
+      const int rest = j >> lcv;
+      const int sb = rest >> 1;
+      const int b0 = (rest & 1) * 32 + b4 * 4;
+      uint4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = rb[(sb * 64 + b0 + u) * PPR + (c >> 2)];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        uint32_t w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = e == 0 ? v[u].x : e == 1 ? v[u].y : e == 2 ? v[u].z : v[u].w;
+        const uint2 re = make_uint2((w[0] & 0xFFFFu) | (w[1] << 16), (w[2] & 0xFFFFu) | (w[3] << 16));
+        const uint2 im = make_uint2((w[0] >> 16) | (w[1] & 0xFFFF0000u), (w[2] >> 16) | (w[3] & 0xFFFF0000u));
+        *reinterpret_cast<uint2*>(turn_raw + ((size_t)sb * CH + c + e) * kTurnRow + 2 * b0) = re;
+        *reinterpret_cast<uint2*>(turn_raw + ((size_t)(S + sb) * CH + c + e) * kTurnRow + 2 * b0) = im;
+      }
+    }
+    __syncthreads();
+    // the rows of this item's channels; threads of channels beyond nch skip
+    // the writes (no barrier inside)
+    write_staged_rows(turn_raw, o, S, nch, CH, c0, kt, jo);
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 cudaError_t launch_tiles(const __half2* spec, const TcTiles& o, int CB, int cb, int S, int G, int nchan,
                          cudaStream_t s) {
   if (cb <= 0) return cudaSuccess;
+  {
+    // persistent form: raw double buffer + staged rows = 800 S CH bytes <= 210 KB
+    int CH = 16;
+    while (CH > 4 && (size_t)800 * S * CH > 210 * 1024) CH /= 2;
+    const size_t smem = (size_t)800 * S * CH;
+    if (smem <= 210 * 1024 && nchan >= 4) {
+      static int sm_count = 0;
+      if (!sm_count) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+          sm_count = 152;
+      }
+      const int ngroups = (nchan + CH - 1) / CH;
+      const int nitems = ngroups * o.NKT * G;
+      cudaError_t e = cudaFuncSetAttribute(k_tiles_p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_tiles_p<<<std::min(nitems, sm_count), 256, smem, s>>>(spec, o, CB, cb, S, nchan, CH, ngroups, nitems);
+      return cudaGetLastError();
+    }
+  }
   // channels per CTA: the staged rows stay within about 100 KB
   int CH = 16;
   while (CH > 4 && (size_t)2 * S * CH * kTurnRow > 100 * 1024) CH /= 2;
