@@ -234,13 +234,28 @@ class Autotuner:
 
     CANDIDATES = (64, 256, 1024, 4096)
 
-    def __init__(self, corr_mod, pool: ReplayPool, device, mem_cap: int):
+    def __init__(self, corr_mod, pool: ReplayPool, device, mem_cap: int, timer: Optional[Callable] = None):
         self.corr = corr_mod
         self.pool = pool
         self.dev = device
         self.mem_cap = int(mem_cap)
         self.cache: Dict[tuple, tuple] = {}  # key -> (chunk blocks, X unit)
         self.trials = 0
+        # timer(handle, out) -> (return code, ms) of one integration; default: CUDA events
+        self.timer = timer or self._time_cuda
+
+    @staticmethod
+    def _time_cuda(c, out):
+        import torch
+        c.correlate_device(out)  # warm: allocation and first launches
+        torch.cuda.synchronize()
+        c.rewind()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc = c.correlate_device(out)
+        e1.record()
+        torch.cuda.synchronize()
+        return rc, e0.elapsed_time(e1)
 
     def key(self, scan, precision):
         blocks = int(round(scan.fs * scan.tint)) // (2 * scan.nchan)
@@ -276,18 +291,10 @@ class Autotuner:
                 for s in range(scan.stations):
                     c.attach_device(s, self.pool.view(s + 1, scan.nsamp[s] * scan.G // 4))
                 c.flush()
-                c.correlate_device(out)  # warm: allocation and first launches
-                torch.cuda.synchronize()
-                c.rewind()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                rc = c.correlate_device(out)
-                e1.record()
-                torch.cuda.synchronize()
+                rc, ms = self.timer(c, out)
                 self.trials += 1
                 if rc != self.corr.CORR_OK:
                     continue
-                ms = e0.elapsed_time(e1)
                 if best_ms is None or ms < best_ms:
                     best, best_ms = (cb, unit), ms
             finally:

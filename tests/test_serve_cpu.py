@@ -135,3 +135,76 @@ def test_scan_mix_shapes():
     b = synth.scan_mix(seed=4, count=96)
     assert [(s.stations, s.nsub, s.npol, s.nchan, s.duration) for s in mix] == \
         [(s.stations, s.nsub, s.npol, s.nchan, s.duration) for s in b]
+
+
+class FakeCorr:
+    """Stands in for the library binding: handles record their settings; the
+    memory a handle needs grows with its chunk length."""
+    CORR_OK = 0
+    CORR_PREC_FP32, CORR_PREC_FP16_TC, CORR_PREC_FP8_TC = 0, 1, 2
+    CORR_X_AUTO, CORR_X_CUDA_CORES, CORR_X_TENSOR_CORES = 0, 1, 2
+
+    def __init__(self, bytes_per_block):
+        self.bytes_per_block = bytes_per_block
+        self.made = []
+
+    def from_scan(self, scan):
+        corr = self
+
+        class H:
+            def __init__(self):
+                self.cfg = {}
+                corr.made.append(self)
+
+            def set_precision(self, p): self.cfg["prec"] = p
+            def set_x_unit(self, u): self.cfg["unit"] = u
+            def set_chunk_blocks(self, cb): self.cfg["cb"] = cb
+            def device_bytes(self): return self.cfg["cb"] * corr.bytes_per_block
+            def attach_device(self, s, view): pass
+            def flush(self): pass
+            def close(self): pass
+        return H()
+
+
+class FakePool:
+    def view(self, off, n):
+        return None
+
+
+class TuneScan:
+    stations, nsub, npol, nchan, fs, tint, G, nbl = 4, 2, 1, 256, 512e3, 1.0, 2, 10
+    nsamp = [512000] * 4
+
+
+def test_autotuner_picks_the_fastest_chunk_and_x_unit_and_caches_it():
+    corr = FakeCorr(bytes_per_block=1 << 20)
+    # a fake timing table: the CUDA cores are faster at long chunks only
+    table = {(64, 1): 5.0, (256, 1): 3.0, (1001, 1): 1.5, (64, 2): 4.0, (256, 2): 2.0, (1001, 2): 2.5}
+
+    def timer(c, out):
+        return corr.CORR_OK, table[(c.cfg["cb"], c.cfg["unit"])]
+
+    tuner = serve.Autotuner(corr, FakePool(), "cpu", mem_cap=1 << 40, timer=timer)
+    sc = TuneScan()
+    # 512e3 / 512 = 1000 blocks per integration, at most 1001 per chunk: candidates 64, 256, 1001
+    assert tuner.config(sc, corr.CORR_PREC_FP16_TC) == (1001, corr.CORR_X_CUDA_CORES)
+    assert tuner.trials == 6
+    assert tuner.choose(sc, corr.CORR_PREC_FP16_TC) == 1001
+    assert tuner.x_unit(sc, corr.CORR_PREC_FP16_TC) == corr.CORR_X_CUDA_CORES
+    assert tuner.trials == 6  # cached
+
+
+def test_autotuner_respects_the_memory_cap_and_fp32_has_one_unit():
+    corr = FakeCorr(bytes_per_block=1 << 20)
+    seen = []
+
+    def timer(c, out):
+        seen.append((c.cfg["cb"], c.cfg["unit"]))
+        return corr.CORR_OK, 100.0 / c.cfg["cb"]  # longer chunks are faster
+
+    # room for 300 blocks of work buffers (plus the output): the 1001-block candidate is skipped
+    tuner = serve.Autotuner(corr, FakePool(), "cpu", mem_cap=300 << 20, timer=timer)
+    cb, unit = tuner.config(TuneScan(), corr.CORR_PREC_FP32)
+    assert (cb, unit) == (256, corr.CORR_X_AUTO)
+    assert {u for _, u in seen} == {corr.CORR_X_AUTO}
+    assert max(b for b, _ in seen) == 256
