@@ -37,10 +37,12 @@ def rel_rms_per_baseline(v, ref):
     return np.sqrt(np.sum(np.abs(v - ref) ** 2, axis=1) / np.sum(np.abs(ref) ** 2, axis=1))
 
 
-def run(corr, sc, streams, nint, precision=0, rotation=1, chunk=0):
+def run(corr, sc, streams, nint, precision=0, rotation=1, chunk=0, unit=None):
     c = corr.from_scan(sc, streams)
     c.set_fringe_rotation(rotation)
     c.set_precision(precision)
+    if unit is not None:
+        c.set_x_unit(unit)
     if chunk:
         c.set_chunk_blocks(chunk)
     outs, ws = [], []
@@ -69,6 +71,18 @@ def cfg2_slice():
 def test_pre_f_config2_slice(corr, cfg2_slice, precision):
     sc, streams, ref, wref = cfg2_slice
     vis, w = run(corr, sc, streams, 2, precision)
+    assert np.array_equal(w, wref)
+    for i in range(2):
+        err = rel_rms_per_baseline(vis[i].reshape(sc.nbl, sc.G, sc.nchan), ref[i])
+        assert np.all(err < TOL[precision]), (precision, i, err.max())
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_pre_f_config2_slice_tensor_cores(corr, cfg2_slice, precision):
+    """Pre-F spectra through the corner turn into tensor-core operand tiles
+    (the default sends 10 stations' FP16 / E4M3 spectra to the CUDA cores)."""
+    sc, streams, ref, wref = cfg2_slice
+    vis, w = run(corr, sc, streams, 2, precision, unit=corr.CORR_X_TENSOR_CORES)
     assert np.array_equal(w, wref)
     for i in range(2):
         err = rel_rms_per_baseline(vis[i].reshape(sc.nbl, sc.G, sc.nchan), ref[i])
