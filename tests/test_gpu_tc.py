@@ -3,10 +3,10 @@ from FP8 (E4M3) spectra, against the FP64 oracle.
 
 Stated bounds, relative RMS per baseline:
   FP16 <= 1e-3: FP16 keeps 11 significant bits; rounding a spectrum value
-       to it leaves a relative error of about 2^-11 / sqrt(3) ~ 2.8e-4 RMS per
-       component, and for noise-dominated baselines the error terms
-       d_a conj(X_b) + X_a conj(d_b) add like the visibility itself, about
-       sqrt(2) x 2e-4 = 3e-4 (measured 3.0-3.5e-4).  A baseline's estimate
+       to it leaves a relative error of about 2.1e-4 RMS per component
+       (tests/test_fp16_bound_cpu.py), and for noise-dominated baselines the
+       error terms d_a conj(X_b) + X_a conj(d_b) add like the visibility
+       itself, about sqrt(2) x 2.1e-4 = 3e-4 (measured 3.0-3.5e-4).  A baseline's estimate
        over only 32 channels scatters by ~1/sqrt(64), and the largest of 2080
        baselines sits ~1.7x above the mean (measured 4.8e-4); 1e-3 leaves 2x
        room above that and still fails a regression of a few ulps.
